@@ -1,0 +1,216 @@
+/*
+ * seraph.h -- C ABI of the B300 streamed-graph engine (Seraph, arXiv 1806.00762).
+ *
+ * The problem this library solves (Sec. 1, Sec. 2.1, Sec. 3.1): a graph larger
+ * than device memory lives in host memory; the GPU processes subgraphs that
+ * stream over the host link while all vertex values stay resident in device
+ * memory.  Subgraphs are CSC pages: a contiguous range of destination vertices
+ * with all of their incoming edges and no destination-index array (Sec. 3.1
+ * "Subgraph Organization").  Each resident page is iterated several times
+ * while the next one is in flight ("Pipelined Subgraph Iteration", Sec. 3.2,
+ * Fig. 4), and vertices predicted to be converged are skipped ("Predictive
+ * Vertex Updating", Sec. 4: strong conditions of Table 1, weak state machine
+ * of Fig. 6).
+ *
+ * Conventions for every call:
+ *   - Return 0 (SERAPH_OK) or a negative SERAPH_E* code; no exception crosses
+ *     the ABI.  seraph_last_error() gives a message for the calling thread.
+ *   - Input arrays are caller-owned and only read during the call (they are
+ *     copied).  Output buffers are caller-owned.  The library owns the pinned
+ *     host pages and every device allocation it makes, and frees them in
+ *     seraph_graph_free / at the end of seraph_run.
+ *   - `mem` says where a pointer lives: SERAPH_MEM_HOST (pageable or pinned
+ *     host memory) or SERAPH_MEM_DEVICE (device memory of the current CUDA
+ *     device, e.g. a torch tensor's data_ptr()).
+ *   - `stream` is a cudaStream_t (NULL = the library's own stream).  Calls are
+ *     synchronous with respect to the host: they return when results are ready.
+ *   - Vertex ids are uint32; n <= 2^32 - 2.  0xFFFFFFFF means "unreachable".
+ *   - Requires a CUDA device of compute capability 10.3 (B300, sm_103a).
+ */
+#ifndef SERAPH_H
+#define SERAPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define SERAPH_OK         0
+#define SERAPH_EINVAL    -1   /* bad argument                                   */
+#define SERAPH_ENOMEM    -2   /* host (pinned) or device allocation failed      */
+#define SERAPH_EBUDGET   -3   /* a page does not fit a ring slot of the budget  */
+#define SERAPH_ECUDA     -4   /* CUDA runtime error (message has the details)   */
+#define SERAPH_ETIMEOUT  -5   /* a bounded wait ran out                         */
+#define SERAPH_EOVERFLOW -6   /* an SSSP distance does not fit below 2^32-1, or
+                                 a page holds 2^32 or more edges                 */
+#define SERAPH_ENOTCONV  -7   /* max_sweeps reached before the fixpoint (SSSP,
+                                 BFS, CC); PageRank stops at max_sweeps with
+                                 SERAPH_OK and stats->converged = 0              */
+
+#define SERAPH_INF 0xFFFFFFFFu
+
+enum seraph_algo { SERAPH_SSSP = 0, SERAPH_BFS = 1, SERAPH_CC = 2, SERAPH_PAGERANK = 3 };
+enum seraph_mem  { SERAPH_MEM_HOST = 0, SERAPH_MEM_DEVICE = 1 };
+/* Predictive vertex updating (Sec. 4). */
+enum seraph_pvu  { SERAPH_PVU_OFF = 0, SERAPH_PVU_STRONG = 1, SERAPH_PVU_WEAK = 2 };
+/* Schedule of the local passes (Sec. 3.2). */
+enum seraph_sched { SERAPH_SCHED_FIXED = 0, SERAPH_SCHED_LEARNED = 1 };
+
+/* Graph flags. */
+#define SERAPH_SYMMETRIZE 1u  /* add (v,u) for every (u,v): the undirected view
+                                 that weakly connected components run on      */
+
+typedef struct seraph_graph seraph_graph;  /* opaque, library-owned */
+
+typedef struct seraph_graph_info {
+    uint64_t n;                 /* vertices                                  */
+    uint64_t m_raw;             /* edges given (after SYMMETRIZE doubling)   */
+    uint64_t m;                 /* edges kept: self-loops dropped, duplicate
+                                   (u,v) collapsed to the smallest weight    */
+    uint64_t struct_bytes;      /* pinned bytes of all page structures       */
+    uint64_t weight_bytes;      /* pinned bytes of all page weights (0 if none) */
+    uint64_t max_page_struct_bytes;
+    uint64_t max_page_weight_bytes;
+    uint32_t num_pages;
+    uint32_t weighted;
+    uint32_t symmetrized;
+    uint32_t max_in_degree;
+} seraph_graph_info;
+
+/*
+ * Build a paged CSC graph from a raw edge list (Sec. 3.1 "Subgraph
+ * Organization").  On the GPU: sort by (destination, source), drop self-loops,
+ * collapse duplicates keeping the smallest weight, build the column offsets,
+ * cut `num_pages` destination ranges balanced on (vertices + in-edges) --
+ * page j starts at the smallest v with (v + in_offset[v]) * P >= j * (n + m)
+ * -- and copy each page into library-owned pinned host memory as
+ *   structure: u32 offsets relative to the page (nv+1, padded to 16 B),
+ *              u32 source ids (ne, padded to 16 B);
+ *   weights:   u32 weights (ne, padded to 16 B), in a separate region so that
+ *              unweighted algorithms stream structure only.
+ * src/dst/w: m entries each in `mem`; w may be NULL (unweighted).  Every id
+ * must be < n (SERAPH_EINVAL otherwise).  Out-degrees are kept resident on the
+ * device for PageRank.  num_pages in [1, 2^20].
+ */
+int seraph_graph_from_edges(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                            const uint32_t* w, int mem, uint32_t flags, uint32_t num_pages,
+                            void* stream, seraph_graph** out);
+
+/* Same, from a CSR (row_off: n+1 uint64 offsets; col: row_off[n] ids; w NULL
+ * or row_off[n] weights), all in `mem`. */
+int seraph_graph_from_csr(uint64_t n, const uint64_t* row_off, const uint32_t* col,
+                          const uint32_t* w, int mem, uint32_t flags, uint32_t num_pages,
+                          void* stream, seraph_graph** out);
+
+int  seraph_graph_get_info(const seraph_graph* g, seraph_graph_info* info);
+
+/* Page boundaries: vb[0..num_pages] (host array of num_pages+1 uint64). */
+int  seraph_graph_page_bounds(const seraph_graph* g, uint64_t* vb);
+
+/* Copy the CSC held in the pinned pages into host arrays (verification):
+ * col_off[n+1] global in-edge offsets, row[m] sources (ascending within each
+ * destination), w[m] weights (may be NULL), out_degree[n] (may be NULL). */
+int  seraph_graph_export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* row,
+                             uint32_t* w, uint32_t* out_degree);
+
+void seraph_graph_free(seraph_graph* g);
+
+/*
+ * Run parameters.  Fill with seraph_params_default(), then override.
+ *
+ * Streaming (Sec. 3.2, Fig. 4): the device edge buffer of `budget_bytes` is a
+ * ring of window+1 slots.  Pages are packed in order into chunks of at most
+ * one slot.  Step t runs `passes` local passes over the `window` most recent
+ * chunks while the next chunk copies into the free slot, then the oldest chunk
+ * leaves the window: with passes = 1 every chunk gets `window` passes per
+ * sweep and shares them with its neighbours (the sliding "super subgraph");
+ * window = 1, passes = k is the double-buffer variant.  If all chunks fit in
+ * the ring at once they are loaded once and never re-streamed.  A sweep is one
+ * step per chunk; every chunk is processed `window * passes` times in it.
+ *
+ * Termination: SSSP/BFS/CC stop after a sweep that ran with prediction off
+ * and changed no value (the all-pull retrieval of Sec. 4.3); PageRank stops
+ * when the FP64 L1 change between two sweep ends is < tol, or at max_sweeps.
+ */
+typedef struct seraph_params {
+    int32_t  algo;              /* seraph_algo                                */
+    uint32_t source;            /* SSSP/BFS source vertex                     */
+    uint64_t budget_bytes;      /* device edge-buffer budget                  */
+    uint32_t window;            /* chunks resident in the compute window, 1..16 */
+    uint32_t passes;            /* local passes per step, 1..64               */
+    int32_t  pvu;               /* seraph_pvu                                 */
+    uint32_t verify;            /* 1: finish with a prediction-off sweep (must
+                                   stay 1 for weak prediction)                */
+    uint8_t  fsm_next[12];      /* weak state machine: next state =
+                                   fsm_next[2*state + changed]; dormant states
+                                   use column 0 as their unconditional tick   */
+    uint8_t  fsm_skip_mask;     /* bit s set: state s skips the update        */
+    uint8_t  kahan;             /* PageRank: 1 = compensated FP32 sums        */
+    uint8_t  pad0[2];
+    uint32_t max_sweeps;
+    double   damping;           /* PageRank d                                 */
+    double   tol;               /* PageRank stop: L1 change < tol             */
+    double   pr_fail_eps;       /* PageRank weak prediction: an update "fails"
+                                   when |dx| <= pr_fail_eps * x               */
+    double   pr_pvu_off_below;  /* PageRank: prediction off once L1 change < this */
+    uint32_t thread_max_deg;    /* in-degree <= this: one thread per vertex   */
+    uint32_t warp_max_deg;      /* <= this: one warp; above: one CTA per vertex */
+    int32_t  sched;             /* seraph_sched                               */
+    uint32_t timeout_ms;        /* bound on every host wait                   */
+    uint32_t profile;           /* 1: time every relax kernel and step with
+                                   CUDA events (fills relax_ms, copy_ms, ...) */
+    uint32_t reserved;
+    void*    sched_model;       /* seraph_sched_model* for SERAPH_SCHED_LEARNED */
+    void*    stream;            /* cudaStream_t for compute, NULL = own       */
+    void*    trace;             /* seraph_trace* to fill, or NULL             */
+} seraph_params;
+
+typedef struct seraph_stats {
+    uint32_t sweeps;            /* sweeps run                                 */
+    uint32_t steps;             /* pipeline steps                             */
+    uint32_t passes_run;        /* local passes executed                      */
+    uint32_t passes_skipped;    /* local passes skipped on the device flag    */
+    uint32_t chunks;            /* chunks per sweep                           */
+    uint32_t resident;          /* 1 if all chunks stayed loaded              */
+    uint32_t converged;         /* 1 if the stop rule was met                 */
+    uint32_t verify_sweeps;     /* sweeps run with prediction off for the stop */
+    uint64_t bytes_streamed;    /* host->device page bytes                    */
+    uint64_t edges_relaxed;     /* in-edges read by attempted vertices        */
+    uint64_t vertices_attempted;
+    uint64_t vertices_skipped;  /* skipped by prediction                      */
+    uint64_t changes;           /* value changes (PageRank: |dx| > eps*x)     */
+    double   time_ms;           /* device time: first copy -> stop decided    */
+    double   copy_ms;           /* sum of copy durations                      */
+    double   compute_ms;        /* sum of step compute durations              */
+    double   wall_ms;           /* host time of the whole call                */
+    double   residual;          /* PageRank: last FP64 L1 change              */
+    double   relax_ms;          /* sum of relax-kernel durations (events)     */
+    uint64_t relax_launches;    /* relax kernels launched                     */
+    uint64_t kernel_launches;   /* all library kernels launched by the run    */
+} seraph_stats;
+
+int seraph_params_default(seraph_params* p, int algo);
+
+/*
+ * Run `p->algo` to its fixpoint over the paged graph.
+ * out_values: n entries in out_mem -- uint32 distances / levels / labels, or
+ * float32 PageRank values.  stats may be NULL.
+ * Errors: SERAPH_EINVAL (bad params, e.g. strong prediction with PageRank, or
+ * source >= n), SERAPH_EBUDGET (a page larger than one ring slot),
+ * SERAPH_EOVERFLOW, SERAPH_ENOTCONV, SERAPH_ETIMEOUT, SERAPH_ECUDA.
+ */
+int seraph_run(seraph_graph* g, const seraph_params* p, void* out_values, int out_mem,
+               seraph_stats* stats);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* seraph_last_error(void);
+
+/* Library version string. */
+const char* seraph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

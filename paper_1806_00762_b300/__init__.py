@@ -1,0 +1,155 @@
+"""Seraph on B300: streamed-graph pipelined subgraph iteration with predictive
+vertex updating (arXiv 1806.00762), as a C-ABI library with a thin Python
+binding.
+
+    g = Graph.from_edges(n, src, dst, w, num_pages=64)     # GPU partitioner
+    values, stats = run(g, "sssp", source=0, budget_bytes=2 << 30, window=4)
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); torch is
+used only for device memory and streams.  All graph work runs in
+libseraph.so (see include/seraph.h).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi as C
+from ._capi import SeraphError, INF
+
+__all__ = ["Graph", "run", "default_params", "SeraphError", "INF", "version"]
+
+
+def version() -> str:
+    return C.lib().seraph_version().decode()
+
+
+def _ptr_mem(a):
+    """(pointer, mem kind, keep-alive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, C.MEM_HOST, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, C.MEM_HOST, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        a = a.contiguous()
+        return a.data_ptr(), (C.MEM_DEVICE if a.is_cuda else C.MEM_HOST), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _is_u32(a) -> bool:
+    if isinstance(a, np.ndarray):
+        return a.dtype == np.uint32
+    return a.element_size() == 4 and not a.is_floating_point()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Graph:
+    """Paged CSC graph in library-owned pinned host memory (Sec. 3.1)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+
+    @classmethod
+    def from_edges(cls, n, src, dst, w=None, symmetrize=False, num_pages=1, stream=None):
+        ps, ms, ks = _ptr_mem(src)
+        pd, md, kd = _ptr_mem(dst)
+        pw, mw, kw = _ptr_mem(w)
+        if ms != md or (w is not None and mw != ms):
+            raise ValueError("src, dst and w must live in the same memory")
+        m = int(len(src))
+        if len(dst) != m or (w is not None and len(w) != m):
+            raise ValueError("src, dst and w must have equal lengths")
+        for arr in (ks, kd, kw):
+            if arr is not None and not _is_u32(arr):
+                raise TypeError("edge arrays must hold 32-bit unsigned integers")
+        out = ctypes.c_void_p()
+        C.check(C.lib().seraph_graph_from_edges(n, m, ps, pd, pw, ms,
+                                                C.SYMMETRIZE if symmetrize else 0, num_pages,
+                                                _stream_ptr(stream), ctypes.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def from_csr(cls, n, row_off, col, w=None, symmetrize=False, num_pages=1, stream=None):
+        pr, mr, kr = _ptr_mem(row_off)
+        pc, mc, kc = _ptr_mem(col)
+        pw, mw, kw = _ptr_mem(w)
+        out = ctypes.c_void_p()
+        C.check(C.lib().seraph_graph_from_csr(n, pr, pc, pw, mr,
+                                              C.SYMMETRIZE if symmetrize else 0, num_pages,
+                                              _stream_ptr(stream), ctypes.byref(out)))
+        return cls(out.value)
+
+    def info(self) -> dict:
+        gi = C.GraphInfo()
+        C.check(C.lib().seraph_graph_get_info(self._h, ctypes.byref(gi)))
+        return {k: getattr(gi, k) for k, _ in gi._fields_}
+
+    def page_bounds(self) -> np.ndarray:
+        vb = np.empty(self.info()["num_pages"] + 1, dtype=np.uint64)
+        C.check(C.lib().seraph_graph_page_bounds(self._h, vb.ctypes.data))
+        return vb
+
+    def export_csc(self):
+        """(col_off, row, w or None, out_degree) copied out of the pinned pages."""
+        i = self.info()
+        col_off = np.empty(i["n"] + 1, dtype=np.uint64)
+        row = np.empty(max(i["m"], 1), dtype=np.uint32)
+        w = np.empty(max(i["m"], 1), dtype=np.uint32) if i["weighted"] else None
+        od = np.empty(i["n"], dtype=np.uint32)
+        C.check(C.lib().seraph_graph_export_csc(self._h, col_off.ctypes.data, row.ctypes.data,
+                                                None if w is None else w.ctypes.data,
+                                                od.ctypes.data))
+        return col_off, row[:i["m"]], (None if w is None else w[:i["m"]]), od
+
+    def free(self):
+        if self._h and self._h.value:
+            C.lib().seraph_graph_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def default_params(algo) -> C.Params:
+    p = C.Params()
+    C.check(C.lib().seraph_params_default(ctypes.byref(p), C.ALGOS[algo] if isinstance(algo, str) else algo))
+    return p
+
+
+def run(graph: Graph, algo, out=None, stream=None, **kw):
+    """Run `algo` ("sssp", "bfs", "cc", "pagerank") to its fixpoint.
+
+    Keyword arguments override fields of seraph_params (e.g. source, window,
+    passes, budget_bytes, pvu="weak").  `out` may be a preallocated numpy
+    array or torch tensor (host or CUDA) of n uint32/float32 values; by
+    default a numpy array is returned.  Returns (values, stats dict)."""
+    p = default_params(algo)
+    for k, v in kw.items():
+        if k == "pvu" and isinstance(v, str):
+            v = C.PVUS[v]
+        if k == "fsm_next":
+            for i, x in enumerate(v):
+                p.fsm_next[i] = int(x)
+            continue
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    p.stream = _stream_ptr(stream)
+    n = graph.info()["n"]
+    if out is None:
+        out = np.empty(n, dtype=np.float32 if p.algo == C.PAGERANK else np.uint32)
+    po, mo, ko = _ptr_mem(out)
+    st = C.Stats()
+    C.check(C.lib().seraph_run(graph._h, ctypes.byref(p), po, mo, ctypes.byref(st)))
+    return out, st.as_dict()

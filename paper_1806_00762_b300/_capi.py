@@ -1,0 +1,116 @@
+"""ctypes mirror of include/seraph.h (structures, prototypes, error codes).
+
+Argument marshalling only: every step of the graph method runs inside
+libseraph.so.  Loading fails loudly when the library is missing -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libseraph.so")
+
+SERAPH_OK = 0
+SERAPH_EINVAL = -1
+SERAPH_ENOMEM = -2
+SERAPH_EBUDGET = -3
+SERAPH_ECUDA = -4
+SERAPH_ETIMEOUT = -5
+SERAPH_EOVERFLOW = -6
+SERAPH_ENOTCONV = -7
+ERROR_NAMES = {
+    SERAPH_EINVAL: "EINVAL", SERAPH_ENOMEM: "ENOMEM", SERAPH_EBUDGET: "EBUDGET",
+    SERAPH_ECUDA: "ECUDA", SERAPH_ETIMEOUT: "ETIMEOUT", SERAPH_EOVERFLOW: "EOVERFLOW",
+    SERAPH_ENOTCONV: "ENOTCONV",
+}
+
+SSSP, BFS, CC, PAGERANK = 0, 1, 2, 3
+ALGOS = {"sssp": SSSP, "bfs": BFS, "cc": CC, "pagerank": PAGERANK, "pr": PAGERANK}
+MEM_HOST, MEM_DEVICE = 0, 1
+PVU_OFF, PVU_STRONG, PVU_WEAK = 0, 1, 2
+PVUS = {"off": PVU_OFF, "strong": PVU_STRONG, "weak": PVU_WEAK}
+SCHED_FIXED, SCHED_LEARNED = 0, 1
+SYMMETRIZE = 1
+INF = 0xFFFFFFFF
+
+u8, u32, i32, u64, dbl, vp = (ctypes.c_uint8, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64,
+                              ctypes.c_double, ctypes.c_void_p)
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", u64), ("m_raw", u64), ("m", u64), ("struct_bytes", u64),
+                ("weight_bytes", u64), ("max_page_struct_bytes", u64),
+                ("max_page_weight_bytes", u64), ("num_pages", u32), ("weighted", u32),
+                ("symmetrized", u32), ("max_in_degree", u32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("algo", i32), ("source", u32), ("budget_bytes", u64), ("window", u32),
+                ("passes", u32), ("pvu", i32), ("verify", u32), ("fsm_next", u8 * 12),
+                ("fsm_skip_mask", u8), ("kahan", u8), ("pad0", u8 * 2), ("max_sweeps", u32),
+                ("damping", dbl), ("tol", dbl), ("pr_fail_eps", dbl),
+                ("pr_pvu_off_below", dbl), ("thread_max_deg", u32), ("warp_max_deg", u32),
+                ("sched", i32), ("timeout_ms", u32), ("profile", u32), ("reserved", u32),
+                ("sched_model", vp), ("stream", vp), ("trace", vp)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("sweeps", u32), ("steps", u32), ("passes_run", u32), ("passes_skipped", u32),
+                ("chunks", u32), ("resident", u32), ("converged", u32), ("verify_sweeps", u32),
+                ("bytes_streamed", u64), ("edges_relaxed", u64), ("vertices_attempted", u64),
+                ("vertices_skipped", u64), ("changes", u64), ("time_ms", dbl),
+                ("copy_ms", dbl), ("compute_ms", dbl), ("wall_ms", dbl), ("residual", dbl),
+                ("relax_ms", dbl), ("relax_launches", u64), ("kernel_launches", u64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# name -> (restype, argtypes); every symbol include/seraph.h declares
+PROTOTYPES = {
+    "seraph_graph_from_edges": (ctypes.c_int, [u64, u64, vp, vp, vp, ctypes.c_int, u32, u32, vp,
+                                               ctypes.POINTER(vp)]),
+    "seraph_graph_from_csr": (ctypes.c_int, [u64, vp, vp, vp, ctypes.c_int, u32, u32, vp,
+                                             ctypes.POINTER(vp)]),
+    "seraph_graph_get_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo)]),
+    "seraph_graph_page_bounds": (ctypes.c_int, [vp, vp]),
+    "seraph_graph_export_csc": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+    "seraph_graph_free": (None, [vp]),
+    "seraph_params_default": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int]),
+    "seraph_run": (ctypes.c_int, [vp, ctypes.POINTER(Params), vp, ctypes.c_int,
+                                  ctypes.POINTER(Stats)]),
+    "seraph_last_error": (ctypes.c_char_p, []),
+    "seraph_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libseraph.so (building it first if it is absent or stale)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libseraph.so missing at {LIB_PATH}; the CUDA path is required")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in PROTOTYPES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SeraphError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(rc: int) -> None:
+    if rc != SERAPH_OK:
+        raise SeraphError(rc, lib().seraph_last_error().decode())

@@ -1,0 +1,171 @@
+// extern "C" entry points of include/seraph.h.  Every call catches
+// exceptions, records a thread-local message and returns a SERAPH_E* code.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "graph.hpp"
+
+namespace seraph {
+int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, seraph_stats* st);
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+int guarded(F&& f) {
+    try {
+        g_last_error.clear();
+        return f();
+    } catch (const seraph::Error& e) {
+        g_last_error = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return SERAPH_ENOMEM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return SERAPH_EINVAL;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return SERAPH_EINVAL;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* seraph_last_error(void) { return g_last_error.c_str(); }
+
+const char* seraph_version(void) { return "seraph-b300 0.1 (sm_103a)"; }
+
+int seraph_graph_from_edges(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                            const uint32_t* w, int mem, uint32_t flags, uint32_t num_pages,
+                            void* stream, seraph_graph** out) {
+    return guarded([&] {
+        SR_CHECK(out != nullptr, SERAPH_EINVAL, "out must not be NULL");
+        *out = nullptr;
+        seraph::Stream s;
+        s.use(stream);
+        seraph_graph* g = new seraph_graph();
+        try {
+            seraph::build_graph(g, n, m, src, dst, w, mem, flags, num_pages, s.s);
+        } catch (...) {
+            delete g;
+            throw;
+        }
+        *out = g;
+        return SERAPH_OK;
+    });
+}
+
+int seraph_graph_from_csr(uint64_t n, const uint64_t* row_off, const uint32_t* col,
+                          const uint32_t* w, int mem, uint32_t flags, uint32_t num_pages,
+                          void* stream, seraph_graph** out) {
+    return guarded([&] {
+        SR_CHECK(out != nullptr, SERAPH_EINVAL, "out must not be NULL");
+        *out = nullptr;
+        seraph::Stream s;
+        s.use(stream);
+        seraph_graph* g = new seraph_graph();
+        try {
+            seraph::build_graph_csr(g, n, row_off, col, w, mem, flags, num_pages, s.s);
+        } catch (...) {
+            delete g;
+            throw;
+        }
+        *out = g;
+        return SERAPH_OK;
+    });
+}
+
+int seraph_graph_get_info(const seraph_graph* g, seraph_graph_info* info) {
+    return guarded([&] {
+        SR_CHECK(g && info, SERAPH_EINVAL, "null argument");
+        std::memset(info, 0, sizeof(*info));
+        info->n = g->n;
+        info->m_raw = g->m_raw;
+        info->m = g->m;
+        info->struct_bytes = g->h_struct.bytes;
+        info->weight_bytes = g->h_weight.bytes;
+        for (const auto& p : g->pages) {
+            info->max_page_struct_bytes = std::max(info->max_page_struct_bytes, p.s_bytes);
+            info->max_page_weight_bytes = std::max(info->max_page_weight_bytes, p.w_bytes);
+        }
+        info->num_pages = g->num_pages;
+        info->weighted = g->weighted;
+        info->symmetrized = g->symmetrized;
+        info->max_in_degree = g->max_in_degree;
+        return SERAPH_OK;
+    });
+}
+
+int seraph_graph_page_bounds(const seraph_graph* g, uint64_t* vb) {
+    return guarded([&] {
+        SR_CHECK(g && vb, SERAPH_EINVAL, "null argument");
+        std::memcpy(vb, g->vb.data(), g->vb.size() * sizeof(uint64_t));
+        return SERAPH_OK;
+    });
+}
+
+int seraph_graph_export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* row, uint32_t* w,
+                            uint32_t* out_degree) {
+    return guarded([&] {
+        SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
+        SR_CHECK(w == nullptr || g->weighted, SERAPH_EINVAL, "graph has no weights");
+        seraph::export_csc(g, col_off, row, w, out_degree);
+        return SERAPH_OK;
+    });
+}
+
+void seraph_graph_free(seraph_graph* g) {
+    if (!g) return;
+    try {
+        cudaSetDevice(g->device);
+        delete g;
+    } catch (...) {
+    }
+}
+
+int seraph_params_default(seraph_params* p, int algo) {
+    return guarded([&] {
+        SR_CHECK(p != nullptr, SERAPH_EINVAL, "null params");
+        std::memset(p, 0, sizeof(*p));
+        p->algo = algo;
+        p->source = 0;
+        p->budget_bytes = 2ull << 30;
+        p->window = 4;
+        p->passes = 1;
+        p->pvu = SERAPH_PVU_OFF;
+        p->verify = 1;
+        // Weak state machine (Fig. 6): 0,1,5 attempt; 2,3,4 are dormant.
+        //   0 -ok-> 0, 0 -fail-> 5;   5 -ok-> 0, 5 -fail-> 3;
+        //   3 -> 2 -> 1 (two dormant passes);  1 -ok-> 0, 1 -fail-> 4;
+        //   4 -> 3 (punishment: one more dormant pass).
+        // Column 1 of a dormant state is its valid-update edge (-> 0).
+        const uint8_t fsm[12] = {5, 0, 4, 0, 1, 0, 2, 0, 3, 0, 3, 0};
+        std::memcpy(p->fsm_next, fsm, 12);
+        p->fsm_skip_mask = (1u << 2) | (1u << 3) | (1u << 4);
+        p->kahan = 1;
+        p->max_sweeps = algo == SERAPH_PAGERANK ? 100 : 1000000;
+        p->damping = 0.85;
+        p->tol = 1e-7;
+        p->pr_fail_eps = 1.0 / (1 << 20);
+        p->pr_pvu_off_below = 1e-6;
+        p->thread_max_deg = 8;
+        p->warp_max_deg = 4096;
+        p->sched = SERAPH_SCHED_FIXED;
+        p->timeout_ms = 600000;
+        return SERAPH_OK;
+    });
+}
+
+int seraph_run(seraph_graph* g, const seraph_params* p, void* out_values, int out_mem,
+               seraph_stats* stats) {
+    return guarded([&] { return seraph::run_graph(g, p, out_values, out_mem, stats); });
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Shared host/device helpers of the seraph library: error handling, RAII
+// buffers, warp/block primitives.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "seraph.h"
+
+namespace seraph {
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define SR_CUDA(x)                                                                     \
+    do {                                                                               \
+        cudaError_t e_ = (x);                                                          \
+        if (e_ != cudaSuccess) {                                                       \
+            if (e_ == cudaErrorMemoryAllocation) (void)cudaGetLastError();             \
+            throw ::seraph::Error(e_ == cudaErrorMemoryAllocation ? SERAPH_ENOMEM      \
+                                                                  : SERAPH_ECUDA,      \
+                                  std::string(#x) + ": " + cudaGetErrorString(e_));    \
+        }                                                                              \
+    } while (0)
+
+#define SR_CHECK(cond, code, msg)                                                      \
+    do {                                                                               \
+        if (!(cond)) throw ::seraph::Error((code), (msg));                             \
+    } while (0)
+
+#define SR_LAUNCH() SR_CUDA(cudaGetLastError())
+
+int device_sms();
+
+// Device allocation owned by the library.
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t count) { alloc(count); }
+    void alloc(size_t count) {
+        release();
+        n = count;
+        if (count) SR_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { release(); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+};
+
+// Pinned host allocation owned by the library.
+struct PinnedBuf {
+    uint8_t* p = nullptr;
+    size_t bytes = 0;
+    void alloc(size_t b) {
+        release();
+        bytes = b;
+        if (b) SR_CUDA(cudaHostAlloc((void**)&p, b, cudaHostAllocPortable));
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    ~PinnedBuf() { release(); }
+};
+
+struct Stream {
+    cudaStream_t s = nullptr;
+    bool owned = false;
+    void create() {
+        SR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        owned = true;
+    }
+    void use(void* ext) {
+        if (ext) { s = (cudaStream_t)ext; owned = false; } else create();
+    }
+    ~Stream() { if (owned && s) cudaStreamDestroy(s); }
+};
+
+inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------- device side
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(kFull, x, o);
+        if ((int)lane_id() >= o) x += y;
+    }
+    return x;
+}
+
+// Block-wide exclusive scan (blockDim.x = NT, multiple of 32).  `ws` must
+// hold NT/32 + 1 elements of shared memory.  Returns the exclusive prefix
+// and writes the block total to *total.
+template <int NT, class T>
+__device__ __forceinline__ T block_excl_scan(T x, T* ws, T* total) {
+    const int warp = threadIdx.x >> 5, nw = NT / 32;
+    T inc = warp_incl_scan(x);
+    if (lane_id() == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T v = lane_id() < (unsigned)nw ? ws[lane_id()] : T(0);
+        T s = warp_incl_scan(v);
+        if (lane_id() < (unsigned)nw) ws[lane_id()] = s - v;
+        if (lane_id() == (unsigned)nw - 1) ws[nw] = s;
+    }
+    __syncthreads();
+    T r = ws[warp] + inc - x;
+    *total = ws[nw];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace seraph

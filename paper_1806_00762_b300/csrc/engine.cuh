@@ -1,0 +1,94 @@
+// Device-side engine of one local pass (Sec. 3.2 pipelined iteration, Sec. 4
+// predictive updating): shared declarations between the kernels (engine.cu)
+// and the host sweep driver (run.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace seraph {
+
+constexpr int kMaxWindow = 16;
+
+// Where a resident page's arrays currently live (device addresses in the
+// edge ring).  Rewritten whenever the page's chunk is (re)loaded.
+struct PageLoc {
+    const uint32_t* off;  // nv+1 page-relative offsets
+    const uint32_t* col;  // ne source ids (16-byte aligned)
+    const uint32_t* w;    // ne weights (16-byte aligned) or null
+    uint32_t vb;          // first vertex
+    uint32_t nv;          // vertices
+};
+
+struct ChunkDesc {
+    uint32_t v_begin, v_end;       // destination range of the chunk
+    uint32_t first_page, end_page; // pages [first, end)
+    uint32_t block_begin;          // first compaction block of this chunk
+    uint32_t pad;
+};
+
+struct WindowDesc {
+    uint32_t nchunks;
+    uint32_t nblocks;              // compaction blocks over all chunks
+    ChunkDesc c[kMaxWindow];
+};
+
+// Counters of one sweep, copied to the host at the sweep boundary.
+struct SweepReport {
+    unsigned long long changed, attempted, skipped, edges;
+    unsigned int overflow, thr_min, passes_run, passes_skipped;
+    double resid, dangling;
+};
+
+struct RunState {
+    SweepReport cur;
+    unsigned int pass_changed[2];
+    unsigned int list_cnt[2][4];
+    unsigned int work[2][4];
+    unsigned int thr_cur, thr_prev, sweeps_done, err;
+    float base, pad;
+    double dsum, rsum;
+};
+
+enum { ALG_SSSP = 0, ALG_BFS = 1, ALG_CC = 2, ALG_PR = 3 };
+
+struct AlgoArgs {
+    uint32_t* val;            // SSSP/BFS/CC values
+    float* x;                 // PageRank values
+    float* contrib;           // x / outdeg (0 for dangling)
+    float* x_next;            // value computed in the current pass
+    const float* inv_out;     // 1 / outdeg or 0
+    uint8_t* state;           // weak-prediction state per vertex
+    RunState* rs;
+    const PageLoc* loc;       // per page
+    const uint32_t* vb;       // page boundaries (P+1)
+    unsigned long long* list[3];  // entries (page << 32) | v, per mapping class
+    uint32_t thread_max, warp_max;
+    float damping, fail_eps;
+    uint8_t fsm_next[12];
+    uint8_t skip_mask;
+    uint8_t pvu;              // SERAPH_PVU_*
+    uint8_t pad[2];
+};
+
+// Launchers (engine.cu).  `pass` is the global pass counter (its parity picks
+// the double-buffered counters); `check_prev` lets the pass exit early on the
+// device when the previous pass of the same step changed nothing;
+// `predict` = 0 runs the pass with prediction off.
+void launch_compact(int algo, const WindowDesc& wd, const AlgoArgs& a, uint32_t pass,
+                    int check_prev, int predict, cudaStream_t s);
+void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, int check_prev,
+                  int grid, cudaStream_t s);
+void launch_pr_apply(const AlgoArgs& a, uint32_t pass, int check_prev, int grid, cudaStream_t s);
+void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t end,
+                     const uint64_t* rel_soff, const uint64_t* rel_woff, const uint64_t* off_bytes,
+                     uint8_t* sbase, uint8_t* wbase, cudaStream_t s);
+void launch_init_values(int algo, const AlgoArgs& a, uint64_t n, uint32_t source,
+                        cudaStream_t s);
+void launch_init_pr(const uint32_t* outdeg, const AlgoArgs& a, float* x_prev, uint64_t n,
+                    cudaStream_t s);
+void launch_close_min(RunState* rs, SweepReport* out, cudaStream_t s);
+void launch_close_pr(const AlgoArgs& a, uint64_t n, float* x_prev, const uint32_t* zero_in,
+                     double damping, double* partial, int nparts, SweepReport* out,
+                     cudaStream_t s);
+
+}  // namespace seraph

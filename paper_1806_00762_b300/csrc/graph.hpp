@@ -1,0 +1,50 @@
+// Internal graph object: the paged CSC of Sec. 3.1 held in pinned host memory,
+// plus the vertex-side arrays that stay resident on the device.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+// Static per-page description.  A page is a contiguous destination range
+// [vb, vb+nv) with all of its in-edges.  In the pinned structure region it is
+//   u32 off[nv+1] (relative to the page's first edge), padded to 16 B,
+//   u32 col[ne] (source ids, ascending per destination), padded to 16 B;
+// its weights (if any) sit at w_off in the separate weight region.
+struct PageMeta {
+    uint64_t vb;        // first vertex
+    uint64_t nv;        // vertices
+    uint64_t ne;        // in-edges
+    uint64_t e0;        // global index of the first in-edge
+    uint64_t s_off;     // byte offset of the page in the structure region
+    uint64_t s_bytes;   // structure bytes (offsets + columns, padded)
+    uint64_t off_bytes; // bytes of the padded offset array
+    uint64_t w_off;     // byte offset in the weight region
+    uint64_t w_bytes;   // weight bytes (padded), 0 if unweighted
+};
+
+struct seraph_graph {
+    int device = 0;
+    uint64_t n = 0, m_raw = 0, m = 0;
+    uint32_t num_pages = 0;
+    bool weighted = false, symmetrized = false;
+    uint32_t max_in_degree = 0;
+    std::vector<PageMeta> pages;
+    std::vector<uint64_t> vb;          // num_pages + 1 page boundaries
+    seraph::PinnedBuf h_struct;        // all page structures, in page order
+    seraph::PinnedBuf h_weight;        // all page weights, in page order
+    seraph::DevBuf<uint32_t> d_outdeg; // out-degree per vertex (PageRank)
+    seraph::DevBuf<uint32_t> d_vb;     // page boundaries (u32) on the device
+    seraph::DevBuf<uint32_t> d_zero_in; // bit v set: v has no in-edge
+};
+
+namespace seraph {
+void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src,
+                 const uint32_t* dst, const uint32_t* w, int mem, uint32_t flags,
+                 uint32_t num_pages, cudaStream_t s);
+void build_graph_csr(seraph_graph* g, uint64_t n, const uint64_t* row_off, const uint32_t* col,
+                     const uint32_t* w, int mem, uint32_t flags, uint32_t num_pages,
+                     cudaStream_t s);
+void export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* row, uint32_t* w,
+                uint32_t* out_degree);
+}  // namespace seraph

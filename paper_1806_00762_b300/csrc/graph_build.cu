@@ -1,0 +1,630 @@
+// Partitioner (Sec. 3.1 "Subgraph Organization"): raw edges -> paged CSC in
+// pinned host memory, all on the GPU.
+//
+//   1. keys = (dst << b) | src per edge (self-loops -> the all-ones marker);
+//   2. stable LSD radix sort of the keys (8-bit digits), weights as payload;
+//   3. drop markers and duplicate keys (keeping the smallest weight);
+//   4. in-edge offsets by binary search of each vertex in the sorted
+//      destinations; out-degrees by atomic counting of the sources;
+//   5. page cut: page j starts at the smallest v with
+//      (v + off[v]) * P >= j * (n + E)  (balanced on vertices + in-edges);
+//   6. page-relative u32 offsets staged on the device, then every page's
+//      offsets / sources / weights copied into the pinned page images.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "graph.hpp"
+
+namespace seraph {
+
+int device_sms() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kItems = 16;
+constexpr uint64_t kTile = kNT * kItems;  // 4096 items per CTA tile
+constexpr uint64_t kMarker = ~0ull;
+
+unsigned grid_for(uint64_t n, int per_block = kNT) {
+    uint64_t b = (n + per_block - 1) / per_block;
+    uint64_t cap = (uint64_t)device_sms() * 32;
+    if (b > cap) b = cap;
+    return (unsigned)std::max<uint64_t>(b, 1);
+}
+
+// ------------------------------------------------------------ device scan
+
+template <class TI>
+__global__ void __launch_bounds__(kNT) scan_reduce_kernel(const TI* __restrict__ in, uint64_t n,
+                                                          uint64_t* __restrict__ sums) {
+    __shared__ uint64_t ws[kNT / 32 + 1];
+    uint64_t base = blockIdx.x * kTile, s = 0;
+    for (int r = 0; r < kItems; ++r) {
+        uint64_t i = base + (uint64_t)r * kNT + threadIdx.x;
+        if (i < n) s += (uint64_t)in[i];
+    }
+    uint64_t tot;
+    block_excl_scan<kNT>(s, ws, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <class TI>
+__global__ void __launch_bounds__(kNT) scan_down_kernel(const TI* in, uint64_t n,
+                                                        const uint64_t* __restrict__ offs,
+                                                        uint64_t* out) {
+    __shared__ uint64_t ws[kNT / 32 + 1];
+    uint64_t base = blockIdx.x * kTile, run = offs[blockIdx.x];
+    for (int r = 0; r < kItems; ++r) {
+        uint64_t i = base + (uint64_t)r * kNT + threadIdx.x;
+        uint64_t x = i < n ? (uint64_t)in[i] : 0;
+        uint64_t tot, ex = block_excl_scan<kNT>(x, ws, &tot);
+        if (i < n) out[i] = run + ex;
+        run += tot;
+    }
+}
+
+// Exclusive scan of n values into uint64 (out may alias in when TI = uint64_t).
+template <class TI>
+void exclusive_scan(const TI* in, uint64_t n, uint64_t* out, cudaStream_t s) {
+    if (n == 0) return;
+    uint64_t nb = (n + kTile - 1) / kTile;
+    DevBuf<uint64_t> offs(nb);
+    if (nb == 1) {
+        SR_CUDA(cudaMemsetAsync(offs.p, 0, sizeof(uint64_t), s));
+    } else {
+        DevBuf<uint64_t> sums(nb);
+        scan_reduce_kernel<TI><<<(unsigned)nb, kNT, 0, s>>>(in, n, sums.p);
+        SR_LAUNCH();
+        exclusive_scan<uint64_t>(sums.p, nb, offs.p, s);
+        SR_CUDA(cudaStreamSynchronize(s));  // sums freed at scope exit
+    }
+    scan_down_kernel<TI><<<(unsigned)nb, kNT, 0, s>>>(in, n, offs.p, out);
+    SR_LAUNCH();
+    SR_CUDA(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------ radix sort
+
+__global__ void __launch_bounds__(kNT) rs_hist_kernel(const uint64_t* __restrict__ keys, uint64_t n,
+                                                      int shift, uint32_t* __restrict__ hist,
+                                                      uint64_t ntiles) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    uint64_t base = blockIdx.x * kTile;
+    for (int r = 0; r < kItems; ++r) {
+        uint64_t i = base + (uint64_t)r * kNT + threadIdx.x;
+        unsigned d = i < n ? (unsigned)(keys[i] >> shift) & 255u : 256u;
+        unsigned peers = __match_any_sync(kFull, d);
+        if (d < 256 && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[d], __popc(peers));
+    }
+    __syncthreads();
+    hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+constexpr size_t kScatterSmem = kTile * 8 + kTile * 4 + 8 * 256 * 4 + 256 * 4 + 256 * 4 +
+                                256 * 8 + (kNT / 32 + 1) * 4;
+
+template <bool HAS_VAL>
+__global__ void __launch_bounds__(kNT) rs_scatter_kernel(const uint64_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin,
+                                                         uint64_t n, int shift,
+                                                         const uint64_t* __restrict__ offs,
+                                                         uint64_t ntiles,
+                                                         uint64_t* __restrict__ kout,
+                                                         uint32_t* __restrict__ vout) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint64_t* s_keys = (uint64_t*)smem;
+    uint32_t* s_vals = (uint32_t*)(s_keys + kTile);
+    uint32_t* s_wcnt = s_vals + kTile;        // [8 warps][256 digits]
+    uint32_t* s_run = s_wcnt + 8 * 256;       // running count per digit
+    uint32_t* s_start = s_run + 256;          // tile-local digit start
+    uint64_t* s_goff = (uint64_t*)(s_start + 256);
+    uint32_t* ws = (uint32_t*)(s_goff + 256);
+
+    const unsigned tid = threadIdx.x, warp = tid >> 5;
+    const uint64_t tile = blockIdx.x, base = tile * kTile;
+    s_run[tid] = 0;
+    s_goff[tid] = offs[(uint64_t)tid * ntiles + tile];
+
+    uint64_t k[kItems];
+    uint32_t v[kItems], rank[kItems];
+    unsigned dg[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        uint64_t i = base + (uint64_t)r * kNT + tid;
+        bool valid = i < n;
+        k[r] = valid ? kin[i] : kMarker;
+        v[r] = (HAS_VAL && valid) ? vin[i] : 0u;
+        dg[r] = valid ? (unsigned)(k[r] >> shift) & 255u : 256u;
+    }
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        for (unsigned j = tid; j < 8 * 256; j += kNT) s_wcnt[j] = 0;
+        __syncthreads();
+        unsigned d = dg[r];
+        unsigned peers = __match_any_sync(kFull, d);
+        unsigned lr = __popc(peers & lanemask_lt());
+        if (d < 256 && lr == 0) s_wcnt[warp * 256 + d] = __popc(peers);
+        __syncthreads();
+        {
+            unsigned run = s_run[tid];
+#pragma unroll
+            for (int w = 0; w < kNT / 32; ++w) {
+                unsigned c = s_wcnt[w * 256 + tid];
+                s_wcnt[w * 256 + tid] = run;
+                run += c;
+            }
+            s_run[tid] = run;
+        }
+        __syncthreads();
+        rank[r] = d < 256 ? s_wcnt[warp * 256 + d] + lr : 0u;
+        __syncthreads();
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan<kNT>(s_run[tid], ws, &tot);
+    s_start[tid] = ex;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        if (dg[r] < 256) {
+            unsigned pos = s_start[dg[r]] + rank[r];
+            s_keys[pos] = k[r];
+            if (HAS_VAL) s_vals[pos] = v[r];
+        }
+    }
+    __syncthreads();
+    uint64_t count = n - base < kTile ? n - base : kTile;
+    for (unsigned j = tid; j < count; j += kNT) {
+        uint64_t key = s_keys[j];
+        unsigned d = (unsigned)(key >> shift) & 255u;
+        uint64_t g = s_goff[d] + (j - s_start[d]);
+        kout[g] = key;
+        if (HAS_VAL) vout[g] = s_vals[j];
+    }
+}
+
+// Sorts keys (and vals) ascending on their low `bits` bits; stable.  On
+// return keys/vals point at the sorted data (buffers may have swapped).
+void radix_sort(DevBuf<uint64_t>& keys, DevBuf<uint64_t>& keys_alt, DevBuf<uint32_t>& vals,
+                DevBuf<uint32_t>& vals_alt, uint64_t n, int bits, cudaStream_t s) {
+    if (n <= 1) return;
+    const bool has_val = vals.p != nullptr;
+    uint64_t ntiles = (n + kTile - 1) / kTile;
+    DevBuf<uint32_t> hist(256 * ntiles);
+    DevBuf<uint64_t> offs(256 * ntiles);
+    static bool attr_set = false;
+    if (!attr_set) {
+        SR_CUDA(cudaFuncSetAttribute(rs_scatter_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kScatterSmem));
+        SR_CUDA(cudaFuncSetAttribute(rs_scatter_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kScatterSmem));
+        attr_set = true;
+    }
+    for (int shift = 0; shift < bits; shift += 8) {
+        rs_hist_kernel<<<(unsigned)ntiles, kNT, 0, s>>>(keys.p, n, shift, hist.p, ntiles);
+        SR_LAUNCH();
+        exclusive_scan<uint32_t>(hist.p, 256 * ntiles, offs.p, s);
+        if (has_val)
+            rs_scatter_kernel<true><<<(unsigned)ntiles, kNT, kScatterSmem, s>>>(
+                keys.p, vals.p, n, shift, offs.p, ntiles, keys_alt.p, vals_alt.p);
+        else
+            rs_scatter_kernel<false><<<(unsigned)ntiles, kNT, kScatterSmem, s>>>(
+                keys.p, nullptr, n, shift, offs.p, ntiles, keys_alt.p, nullptr);
+        SR_LAUNCH();
+        std::swap(keys, keys_alt);
+        if (has_val) std::swap(vals, vals_alt);
+    }
+    SR_CUDA(cudaStreamSynchronize(s));
+}
+
+// ----------------------------------------------------------- build steps
+
+__global__ void check_ids_kernel(const uint32_t* __restrict__ a, uint64_t m, uint64_t n,
+                                 unsigned* bad) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        if (a[i] >= n) atomicOr(bad, 1u);
+}
+
+__global__ void make_keys_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                                 const uint32_t* __restrict__ w, uint64_t m, int b, bool sym,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t u = src[i], v = dst[i];
+        uint64_t k = u == v ? kMarker : (v << b) | u;
+        keys[i] = k;
+        if (vals) vals[i] = w[i];
+        if (sym) {
+            keys[m + i] = u == v ? kMarker : (u << b) | v;
+            if (vals) vals[m + i] = w[i];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kNT) dedupe_count_kernel(const uint64_t* __restrict__ keys,
+                                                           uint64_t n, uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t ws[kNT / 32 + 1];
+    uint64_t base = blockIdx.x * kTile;
+    uint32_t c = 0;
+    for (int r = 0; r < kItems; ++r) {
+        uint64_t i = base + (uint64_t)r * kNT + threadIdx.x;
+        if (i < n) {
+            uint64_t k = keys[i];
+            c += (k != kMarker && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+        }
+    }
+    uint32_t tot;
+    block_excl_scan<kNT>(c, ws, &tot);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kNT) dedupe_write_kernel(
+    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n,
+    const uint64_t* __restrict__ tile_off, int b, uint32_t* __restrict__ col,
+    uint32_t* __restrict__ dcol, uint32_t* __restrict__ wout) {
+    __shared__ uint32_t ws[kNT / 32 + 1];
+    const uint64_t base = blockIdx.x * kTile;
+    const uint64_t mask = (1ull << b) - 1;
+    uint64_t run = tile_off[blockIdx.x];
+    for (int r = 0; r < kItems; ++r) {
+        uint64_t i = base + (uint64_t)r * kNT + threadIdx.x;
+        uint64_t k = i < n ? keys[i] : kMarker;
+        uint32_t keep = (i < n && k != kMarker && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+        uint32_t tot, ex = block_excl_scan<kNT>(keep, ws, &tot);
+        if (keep) {
+            uint64_t pos = run + ex;
+            col[pos] = (uint32_t)(k & mask);
+            dcol[pos] = (uint32_t)(k >> b);
+            if (vals) {
+                uint32_t wm = vals[i];
+                for (uint64_t j = i + 1; j < n && keys[j] == k; ++j) wm = min(wm, vals[j]);
+                wout[pos] = wm;
+            }
+        }
+        run += tot;
+    }
+}
+
+__global__ void col_off_kernel(const uint32_t* __restrict__ dcol, uint64_t E, uint64_t n,
+                               uint64_t* __restrict__ col_off) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v <= n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t lo = 0, hi = E;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if ((uint64_t)dcol[mid] < v) lo = mid + 1; else hi = mid;
+        }
+        col_off[v] = lo;
+    }
+}
+
+__global__ void outdeg_kernel(const uint32_t* __restrict__ col, uint64_t E,
+                              uint32_t* __restrict__ outdeg) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(&outdeg[col[i]], 1u);
+}
+
+__global__ void max_indeg_kernel(const uint64_t* __restrict__ col_off, uint64_t n, unsigned* mx) {
+    unsigned local = 0;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t d = col_off[v + 1] - col_off[v];
+        local = max(local, d > 0xFFFFFFFFull ? 0xFFFFFFFFu : (unsigned)d);
+    }
+    local = __reduce_max_sync(kFull, local);
+    if (lane_id() == 0) atomicMax(mx, local);
+}
+
+__global__ void zero_in_kernel(const uint64_t* __restrict__ col_off, uint64_t n,
+                               uint32_t* __restrict__ bits) {
+    const uint64_t words = (n + 31) / 32;
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t m = 0;
+        for (uint32_t j = 0; j < 32; ++j) {
+            uint64_t v = 32 * w + j;
+            if (v < n && col_off[v + 1] == col_off[v]) m |= 1u << j;
+        }
+        bits[w] = m;
+    }
+}
+
+__global__ void page_cut_kernel(const uint64_t* __restrict__ col_off, uint64_t n, uint32_t P,
+                                uint64_t* __restrict__ vb) {
+    const uint64_t total = n + col_off[n];
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j <= P;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        if (j == 0) { vb[0] = 0; continue; }
+        if (j == P) { vb[P] = n; continue; }
+        uint64_t lo = 0, hi = n, target = j * total;
+        while (lo < hi) {  // smallest v in [0, n] with (v + off[v]) * P >= j * total
+            uint64_t mid = (lo + hi) >> 1;
+            if ((mid + col_off[mid]) * (uint64_t)P >= target) hi = mid; else lo = mid + 1;
+        }
+        vb[j] = lo;
+    }
+}
+
+__global__ void gather_off_kernel(const uint64_t* __restrict__ col_off,
+                                  const uint64_t* __restrict__ vb, uint32_t P,
+                                  uint64_t* __restrict__ eb) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j <= P;
+         j += (uint64_t)gridDim.x * blockDim.x)
+        eb[j] = col_off[vb[j]];
+}
+
+// Page-relative offsets: stage[st[p] + i] = off[vb_p + i] - off[vb_p], i in [0, nv_p].
+__global__ void stage_off_kernel(const uint64_t* __restrict__ col_off,
+                                 const uint64_t* __restrict__ vb, const uint64_t* __restrict__ st,
+                                 uint32_t P, uint64_t n, uint32_t* __restrict__ stage) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v <= n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        // page p owning v: largest p with vb[p] <= v, p < P (v = n closes page P-1)
+        uint32_t lo = 0, hi = P - 1;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) >> 1;
+            if (vb[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        uint32_t p = lo;
+        stage[st[p] + (v - vb[p])] = (uint32_t)(col_off[v] - col_off[vb[p]]);
+        // a vertex that closes page p-1 (v == vb[p], p > 0) also writes its end
+        if (v == vb[p] && p > 0) {
+            uint32_t q = p - 1;
+            while (true) {  // pages q with vb[q+1] == v (several if some are empty)
+                stage[st[q] + (v - vb[q])] = (uint32_t)(col_off[v] - col_off[vb[q]]);
+                if (q == 0 || vb[q] != v) break;
+                --q;
+            }
+        }
+    }
+}
+
+__global__ void expand_csr_kernel(const uint64_t* __restrict__ row_off, uint64_t n,
+                                  uint32_t* __restrict__ src) {
+    uint64_t E = row_off[n];
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t lo = 0, hi = n - 1;  // largest u with row_off[u] <= e
+        while (lo < hi) {
+            uint64_t mid = (lo + hi + 1) >> 1;
+            if (row_off[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        src[e] = (uint32_t)lo;
+    }
+}
+
+int bits_for(uint64_t n) {
+    int b = 1;
+    while (b < 64 && (1ull << b) < n) ++b;
+    return b;
+}
+
+template <class T>
+const T* to_device(const T* p, uint64_t count, int mem, DevBuf<T>& hold, cudaStream_t s) {
+    if (mem == SERAPH_MEM_DEVICE || p == nullptr) return p;
+    hold.alloc(count);
+    if (count) SR_CUDA(cudaMemcpyAsync(hold.p, p, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    return hold.p;
+}
+
+}  // namespace
+
+void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in,
+                 const uint32_t* dst_in, const uint32_t* w_in, int mem, uint32_t flags,
+                 uint32_t P, cudaStream_t s) {
+    SR_CHECK(n >= 1 && n <= 0xFFFFFFFEull, SERAPH_EINVAL, "n must be in [1, 2^32-2]");
+    SR_CHECK(P >= 1 && P <= (1u << 20), SERAPH_EINVAL, "num_pages must be in [1, 2^20]");
+    SR_CHECK(mem == SERAPH_MEM_HOST || mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad mem kind");
+    SR_CHECK(m == 0 || (src_in && dst_in), SERAPH_EINVAL, "src/dst must not be NULL");
+    SR_CHECK(m < (1ull << 36), SERAPH_EINVAL, "too many edges");
+    const bool sym = flags & SERAPH_SYMMETRIZE;
+    const bool weighted = w_in != nullptr;
+    SR_CUDA(cudaGetDevice(&g->device));
+    g->n = n;
+    g->m_raw = sym ? 2 * m : m;
+    g->num_pages = P;
+    g->weighted = weighted;
+    g->symmetrized = sym;
+
+    const uint64_t M = g->m_raw;
+    const int b = bits_for(n);
+    DevBuf<uint64_t> keys(M), keys_alt(M);
+    DevBuf<uint32_t> vals, vals_alt;
+    if (weighted) { vals.alloc(M); vals_alt.alloc(M); }
+    {
+        DevBuf<uint32_t> hs, hd, hw;
+        const uint32_t* src = to_device(src_in, m, mem, hs, s);
+        const uint32_t* dst = to_device(dst_in, m, mem, hd, s);
+        const uint32_t* w = to_device(w_in, m, mem, hw, s);
+        if (m) {
+            DevBuf<unsigned> bad(1);
+            SR_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+            check_ids_kernel<<<grid_for(m), kNT, 0, s>>>(src, m, n, bad.p);
+            check_ids_kernel<<<grid_for(m), kNT, 0, s>>>(dst, m, n, bad.p);
+            SR_LAUNCH();
+            unsigned hb = 0;
+            SR_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+            SR_CUDA(cudaStreamSynchronize(s));
+            SR_CHECK(hb == 0, SERAPH_EINVAL, "an edge endpoint is >= n");
+            make_keys_kernel<<<grid_for(m), kNT, 0, s>>>(src, dst, w, m, b, sym, keys.p, vals.p);
+            SR_LAUNCH();
+        }
+        SR_CUDA(cudaStreamSynchronize(s));
+    }
+    radix_sort(keys, keys_alt, vals, vals_alt, M, 2 * b, s);
+    keys_alt.release();
+    vals_alt.release();
+
+    // dedupe + compaction
+    uint64_t ntiles = (M + kTile - 1) / kTile;
+    uint64_t E = 0;
+    DevBuf<uint32_t> col, dcol, wcol;
+    if (M) {
+        DevBuf<uint32_t> cnt(ntiles);
+        DevBuf<uint64_t> toff(ntiles + 1);
+        dedupe_count_kernel<<<(unsigned)ntiles, kNT, 0, s>>>(keys.p, M, cnt.p);
+        SR_LAUNCH();
+        exclusive_scan<uint32_t>(cnt.p, ntiles, toff.p, s);
+        uint64_t last_off = 0;
+        uint32_t last_cnt = 0;
+        SR_CUDA(cudaMemcpyAsync(&last_off, toff.p + ntiles - 1, 8, cudaMemcpyDeviceToHost, s));
+        SR_CUDA(cudaMemcpyAsync(&last_cnt, cnt.p + ntiles - 1, 4, cudaMemcpyDeviceToHost, s));
+        SR_CUDA(cudaStreamSynchronize(s));
+        E = last_off + last_cnt;
+        col.alloc(std::max<uint64_t>(E, 1));
+        dcol.alloc(std::max<uint64_t>(E, 1));
+        if (weighted) wcol.alloc(std::max<uint64_t>(E, 1));
+        dedupe_write_kernel<<<(unsigned)ntiles, kNT, 0, s>>>(keys.p, vals.p, M, toff.p, b, col.p,
+                                                             dcol.p, wcol.p);
+        SR_LAUNCH();
+        SR_CUDA(cudaStreamSynchronize(s));
+    }
+    keys.release();
+    vals.release();
+    g->m = E;
+
+    DevBuf<uint64_t> col_off(n + 1);
+    col_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(dcol.p, E, n, col_off.p);
+    SR_LAUNCH();
+    dcol.release();
+    g->d_zero_in.alloc((n + 31) / 32);
+    zero_in_kernel<<<grid_for((n + 31) / 32), kNT, 0, s>>>(col_off.p, n, g->d_zero_in.p);
+    SR_LAUNCH();
+    g->d_outdeg.alloc(n);
+    SR_CUDA(cudaMemsetAsync(g->d_outdeg.p, 0, n * sizeof(uint32_t), s));
+    if (E) {
+        outdeg_kernel<<<grid_for(E), kNT, 0, s>>>(col.p, E, g->d_outdeg.p);
+        SR_LAUNCH();
+    }
+    {
+        DevBuf<unsigned> mx(1);
+        SR_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned), s));
+        max_indeg_kernel<<<grid_for(n), kNT, 0, s>>>(col_off.p, n, mx.p);
+        SR_LAUNCH();
+        SR_CUDA(cudaMemcpyAsync(&g->max_in_degree, mx.p, 4, cudaMemcpyDeviceToHost, s));
+    }
+
+    // page cut
+    DevBuf<uint64_t> d_vb(P + 1), d_eb(P + 1);
+    page_cut_kernel<<<grid_for(P + 1), kNT, 0, s>>>(col_off.p, n, P, d_vb.p);
+    gather_off_kernel<<<grid_for(P + 1), kNT, 0, s>>>(col_off.p, d_vb.p, P, d_eb.p);
+    SR_LAUNCH();
+    g->vb.resize(P + 1);
+    std::vector<uint64_t> eb(P + 1);
+    SR_CUDA(cudaMemcpyAsync(g->vb.data(), d_vb.p, (P + 1) * 8, cudaMemcpyDeviceToHost, s));
+    SR_CUDA(cudaMemcpyAsync(eb.data(), d_eb.p, (P + 1) * 8, cudaMemcpyDeviceToHost, s));
+    SR_CUDA(cudaStreamSynchronize(s));
+
+    g->pages.resize(P);
+    std::vector<uint64_t> st(P + 1);
+    uint64_t s_off = 0, w_off = 0, stage_n = 0;
+    for (uint32_t p = 0; p < P; ++p) {
+        PageMeta& pm = g->pages[p];
+        pm.vb = g->vb[p];
+        pm.nv = g->vb[p + 1] - g->vb[p];
+        pm.e0 = eb[p];
+        pm.ne = eb[p + 1] - eb[p];
+        SR_CHECK(pm.ne < 0xFFFFFFFFull, SERAPH_EOVERFLOW, "a page holds 2^32 or more edges");
+        pm.off_bytes = align_up(4 * (pm.nv + 1), 16);
+        pm.s_bytes = pm.off_bytes + align_up(4 * pm.ne, 16);
+        pm.w_bytes = weighted ? align_up(4 * pm.ne, 16) : 0;
+        pm.s_off = s_off;
+        pm.w_off = w_off;
+        s_off += pm.s_bytes;
+        w_off += pm.w_bytes;
+        st[p] = stage_n;
+        stage_n += pm.nv + 1;
+    }
+    st[P] = stage_n;
+    g->d_vb.alloc(P + 1);
+    {
+        std::vector<uint32_t> vb32(P + 1);
+        for (uint32_t p = 0; p <= P; ++p) vb32[p] = (uint32_t)g->vb[p];
+        SR_CUDA(cudaMemcpyAsync(g->d_vb.p, vb32.data(), (P + 1) * 4, cudaMemcpyHostToDevice, s));
+        SR_CUDA(cudaStreamSynchronize(s));
+    }
+
+    DevBuf<uint64_t> d_st(P + 1);
+    DevBuf<uint32_t> stage(stage_n);
+    SR_CUDA(cudaMemcpyAsync(d_st.p, st.data(), (P + 1) * 8, cudaMemcpyHostToDevice, s));
+    stage_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(col_off.p, d_vb.p, d_st.p, P, n, stage.p);
+    SR_LAUNCH();
+
+    g->h_struct.alloc(s_off);
+    if (weighted) g->h_weight.alloc(w_off);
+    for (uint32_t p = 0; p < P; ++p) {
+        const PageMeta& pm = g->pages[p];
+        uint8_t* hs = g->h_struct.p + pm.s_off;
+        SR_CUDA(cudaMemcpyAsync(hs, stage.p + st[p], 4 * (pm.nv + 1), cudaMemcpyDeviceToHost, s));
+        std::memset(hs + 4 * (pm.nv + 1), 0, pm.off_bytes - 4 * (pm.nv + 1));
+        if (pm.ne)
+            SR_CUDA(cudaMemcpyAsync(hs + pm.off_bytes, col.p + pm.e0, 4 * pm.ne,
+                                    cudaMemcpyDeviceToHost, s));
+        std::memset(hs + pm.off_bytes + 4 * pm.ne, 0, pm.s_bytes - pm.off_bytes - 4 * pm.ne);
+        if (weighted) {
+            uint8_t* hw = g->h_weight.p + pm.w_off;
+            if (pm.ne)
+                SR_CUDA(cudaMemcpyAsync(hw, wcol.p + pm.e0, 4 * pm.ne, cudaMemcpyDeviceToHost, s));
+            std::memset(hw + 4 * pm.ne, 0, pm.w_bytes - 4 * pm.ne);
+        }
+    }
+    SR_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_graph_csr(seraph_graph* g, uint64_t n, const uint64_t* row_off_in, const uint32_t* col_in,
+                     const uint32_t* w_in, int mem, uint32_t flags, uint32_t P, cudaStream_t s) {
+    SR_CHECK(n >= 1 && n <= 0xFFFFFFFEull, SERAPH_EINVAL, "n must be in [1, 2^32-2]");
+    SR_CHECK(row_off_in != nullptr, SERAPH_EINVAL, "row_off must not be NULL");
+    uint64_t m = 0;
+    if (mem == SERAPH_MEM_DEVICE) {
+        SR_CUDA(cudaMemcpyAsync(&m, row_off_in + n, 8, cudaMemcpyDeviceToHost, s));
+        SR_CUDA(cudaStreamSynchronize(s));
+    } else {
+        m = row_off_in[n];
+    }
+    DevBuf<uint64_t> hro;
+    DevBuf<uint32_t> hc, hw;
+    const uint64_t* row_off = to_device(row_off_in, n + 1, mem, hro, s);
+    const uint32_t* col = to_device(col_in, m, mem, hc, s);
+    const uint32_t* w = to_device(w_in, m, mem, hw, s);
+    DevBuf<uint32_t> src(std::max<uint64_t>(m, 1));
+    if (m) {
+        expand_csr_kernel<<<grid_for(m), kNT, 0, s>>>(row_off, n, src.p);
+        SR_LAUNCH();
+    }
+    SR_CUDA(cudaStreamSynchronize(s));
+    build_graph(g, n, m, src.p, col, w, SERAPH_MEM_DEVICE, flags, P, s);
+}
+
+void export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* row, uint32_t* w,
+                uint32_t* out_degree) {
+    for (uint32_t p = 0; p < g->num_pages; ++p) {
+        const PageMeta& pm = g->pages[p];
+        const uint32_t* off = (const uint32_t*)(g->h_struct.p + pm.s_off);
+        const uint32_t* c = (const uint32_t*)(g->h_struct.p + pm.s_off + pm.off_bytes);
+        if (col_off)
+            for (uint64_t i = 0; i < pm.nv; ++i) col_off[pm.vb + i] = pm.e0 + off[i];
+        if (row && pm.ne) std::memcpy(row + pm.e0, c, 4 * pm.ne);
+        if (w && g->weighted && pm.ne)
+            std::memcpy(w + pm.e0, g->h_weight.p + pm.w_off, 4 * pm.ne);
+    }
+    if (col_off) col_off[g->n] = g->m;
+    if (out_degree) {
+        SR_CUDA(cudaMemcpy(out_degree, g->d_outdeg.p, g->n * 4, cudaMemcpyDeviceToHost));
+    }
+}
+
+}  // namespace seraph

@@ -1,0 +1,87 @@
+"""CPU-side checks of the C ABI: the library loads without a GPU, exports every
+symbol include/seraph.h declares, and the ctypes mirror has the C layout.
+No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1806_00762_b300 as seraph
+from paper_1806_00762_b300 import _capi as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "seraph.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(seraph_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    names = declared_functions()
+    assert "seraph_run" in names and "seraph_graph_from_edges" in names
+    lib = C.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in C.PROTOTYPES, name
+
+
+def _c_layout(struct, fields):
+    src = f"""
+#include <stdio.h>
+#include <stddef.h>
+#include "seraph.h"
+int main(void) {{
+  printf("%zu\\n", sizeof({struct}));
+  {''.join(f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)}
+  return 0;
+}}"""
+    d = os.path.join(ROOT, "_build")
+    os.makedirs(d, exist_ok=True)
+    c = os.path.join(d, f"layout_{struct}.c")
+    exe = c[:-2]
+    open(c, "w").write(src)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    return [int(x) for x in out]
+
+
+@pytest.mark.parametrize("name,cls", [("seraph_params", C.Params), ("seraph_stats", C.Stats),
+                                      ("seraph_graph_info", C.GraphInfo)])
+def test_struct_layout_matches_header(name, cls):
+    fields = [f for f, _ in cls._fields_ if not f.startswith("pad")]
+    got = _c_layout(name, fields)
+    assert got[0] == ctypes.sizeof(cls)
+    for f, off in zip(fields, got[1:]):
+        assert getattr(cls, f).offset == off, f
+
+
+def test_params_default_without_gpu():
+    p = seraph.default_params("pagerank")
+    assert p.algo == C.PAGERANK and p.max_sweeps == 100 and abs(p.damping - 0.85) < 1e-15
+    assert p.tol == 1e-7 and p.kahan == 1 and p.verify == 1
+    # weak state machine: 0,1,5 attempt, 2,3,4 dormant
+    assert p.fsm_skip_mask == 0b011100
+    nxt = list(p.fsm_next)
+    assert (nxt[0], nxt[1]) == (5, 0) and (nxt[10], nxt[11]) == (3, 0)
+    assert (nxt[6], nxt[4], nxt[2]) == (2, 1, 4)
+
+
+def test_null_arguments_are_rejected_with_message():
+    lib = C.lib()
+    rc = lib.seraph_run(None, None, None, 0, None)
+    assert rc == C.SERAPH_EINVAL
+    assert b"null" in lib.seraph_last_error()
+    assert lib.seraph_params_default(None, 0) == C.SERAPH_EINVAL
+
+
+def test_input_module_and_oracle_libraries_load():
+    import oracle
+    import synth
+    synth._dev_lib()
+    oracle._L()
+    assert hasattr(synth._dev_lib(), "synth_rmat_device")
