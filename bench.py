@@ -1,0 +1,311 @@
+"""Benchmark: time-to-fixpoint and effective GTEPS of the streamed Seraph hot
+path on R-MAT-28 (2^28 vertices, edge factor 16, a,b,c,d = .57,.19,.19,.05),
+512 destination-range pages in pinned host memory, a 16 GB device edge-buffer
+budget, vertex arrays resident in HBM, SSSP (uint32 weights in [1,255], from
+vertex 0) and PageRank (FP32 Kahan sums, FP64 residual, L1 < 1e-7 or 100
+sweeps), predictive vertex updating on (weak state machine), fixed schedule
+with k = 4 local iterations per resident chunk.
+
+One step = SSSP to its fixpoint + PageRank to its stop rule.  `value` is the
+effective GTEPS of the step (edges of the graph, counted once per algorithm,
+over the device-measured time from the first page copy to the stop
+decision).  `e2e` is the same through the public call with host output
+buffers, timed on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl seraph|reference]
+
+Under torchrun every rank runs an independent replica (the method is
+single-GPU); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-fixpoint and effective GTEPS, RMAT-28 streamed; learned vs fixed sched"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="seraph", choices=["seraph", "reference"])
+    ap.add_argument("--scale", type=int, default=28)
+    ap.add_argument("--pages", type=int, default=512)
+    ap.add_argument("--budget-gb", type=float, default=16.0)
+    ap.add_argument("--window", type=int, default=4)
+    ap.add_argument("--passes", type=int, default=1)
+    ap.add_argument("--pvu", default="weak")
+    ap.add_argument("--cpu-scale", type=int, default=22, help="R-MAT scale of the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self) -> dict:
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------- setup
+
+def link_gbps(torch, nbytes=1 << 30, reps=5, chunks=4) -> float:
+    """Pinned host->device copy bandwidth: 4 x 1 GiB, best of 5."""
+    h = torch.empty(chunks * nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(chunks * nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    best = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        with torch.cuda.stream(s):
+            for i in range(chunks):
+                d[i * nbytes:(i + 1) * nbytes].copy_(h[i * nbytes:(i + 1) * nbytes], non_blocking=True)
+        e1.record(s)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del h, d
+    return chunks * nbytes / (best / 1e3) / 1e9
+
+
+def build_graph(seraph, synth, torch, scale, pages):
+    n = 1 << scale
+    m = synth.rmat_config(scale).m
+    src = torch.empty(m, dtype=torch.int32, device="cuda")
+    dst = torch.empty_like(src)
+    w = torch.empty_like(src)
+    synth.rmat_edges_device(scale, src.data_ptr(), dst.data_ptr(), w.data_ptr())
+    torch.cuda.synchronize()
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=pages)
+    del src, dst, w
+    torch.cuda.empty_cache()
+    return g
+
+
+def algo_bytes(algo, st) -> float:
+    """Algorithmic bytes of the relax kernels of a run:
+    SSSP 12 B/edge (column, weight, gathered distance) + 16 B per attempted
+    vertex (list entry, offset, old value) + 4 B per change; PageRank 8 B/edge
+    (column, gathered contribution) + 20 B per attempted vertex (list entry,
+    offset, old value, new value); +2 B per attempted vertex for the weak
+    prediction state."""
+    E, V, ch = st["edges_relaxed"], st["vertices_attempted"], st["changes"]
+    if algo == "sssp":
+        return 12 * E + 16 * V + 4 * ch + 2 * V
+    return 8 * E + 20 * V + 2 * V
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_sample(scale, steps=1):
+    """The oracle as it stands on an R-MAT sample of the same family:
+    Dijkstra (1 thread) and FP64 PageRank with the same stop rule as the GPU
+    (OpenMP over vertices).  Returns (GTEPS, seconds, description, threads)."""
+    import oracle
+    import synth
+    n = 1 << scale
+    src, dst = synth.rmat_edges(scale)
+    w = synth.weights(src, dst)
+    og = oracle.build_csr(n, src, dst, w)
+    del src, dst, w
+    total_t, total_e = 0.0, 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.sssp(og, 0)
+        t1 = time.perf_counter()
+        oracle.pagerank(og, tol=1e-7, maxit=100)
+        t2 = time.perf_counter()
+        total_t += t2 - t0
+        total_e += 2 * og.m
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"RMAT-{scale} (same generator and shape, {og.m} edges): oracle Dijkstra from vertex 0 "
+            f"(1 thread) + FP64 PageRank to L1<1e-7 ({threads} OpenMP threads); GTEPS scaled as "
+            f"edges per algorithm / time")
+    return total_e / total_t / 1e9, total_t, desc, threads
+
+
+# --------------------------------------------------------------------- main
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": f"rmat{args.scale}-ef16-streamed", "scale": args.scale, "edge_factor": 16,
+              "pages": args.pages, "budget_gb": args.budget_gb, "window": args.window,
+              "passes": args.passes, "pvu": args.pvu, "algorithms": ["sssp", "pagerank"],
+              "schedule": "fixed", "inputs": "pinned host pages streamed each sweep (the method)",
+              "l2_flush": "inputs larger than L2 (graph >= 2 GB per sweep)",
+              "parallelism": f"replicas{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle  # noqa: F401  (the reference arm is the CPU oracle)
+        sample_scale = args.cpu_scale
+        for _ in range(args.warmup):
+            cpu_oracle_sample(sample_scale)
+        g_s, t_s, desc, thr = cpu_oracle_sample(sample_scale, steps=args.steps)
+        line = {"metric": METRIC, "value": g_s, "unit": "GTEPS", "n_gpus": 0, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_s / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32+f64",
+                "data": "synthetic", "config": config, "impl": "reference",
+                "cpu_baseline": {"value": g_s, "unit": "GTEPS", "cores": thr, "kind": "oracle",
+                                 "sample": desc},
+                "e2e": {"value": g_s, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import synth
+    import paper_1806_00762_b300 as seraph
+
+    t_setup = time.time()
+    g = build_graph(seraph, synth, torch, args.scale, args.pages)
+    info = g.info()
+    E = info["m"]
+    n = info["n"]
+    setup_s = time.time() - t_setup
+    link = link_gbps(torch)
+    budget = int(args.budget_gb * (1 << 30))
+    common = dict(budget_bytes=budget, window=args.window, passes=args.passes, pvu=args.pvu,
+                  profile=1)
+    out_u = np.empty(n, dtype=np.uint32)
+    out_f = np.empty(n, dtype=np.float32)
+
+    def step():
+        _, s1 = seraph.run(g, "sssp", out=out_u, source=0, **common)
+        _, s2 = seraph.run(g, "pagerank", out=out_f, **common)
+        return s1, s2
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    stats = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            stats.append(step())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+
+    dev_s = sum(s1["time_ms"] + s2["time_ms"] for s1, s2 in stats) / 1e3
+    wall_calls_s = sum(s1["wall_ms"] + s2["wall_ms"] for s1, s2 in stats) / 1e3
+    if world > 1:
+        tt = torch.tensor([dev_s, wall_calls_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        dev_s, wall_calls_s = float(tt[0]), float(tt[1])
+    units = 2 * E * args.steps * world
+    value = units / dev_s / 1e9
+    e2e = units / wall_calls_s / 1e9
+    relax_bytes = sum(algo_bytes("sssp", s1) + algo_bytes("pagerank", s2) for s1, s2 in stats)
+    relax_ms = sum(s1["relax_ms"] + s2["relax_ms"] for s1, s2 in stats)
+    relax_launches = sum(s1["relax_launches"] + s2["relax_launches"] for s1, s2 in stats)
+    streamed = sum(s1["bytes_streamed"] + s2["bytes_streamed"] for s1, s2 in stats)
+    copy_ms = sum(s1["copy_ms"] + s2["copy_ms"] for s1, s2 in stats)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    achieved = relax_bytes / (relax_ms / 1e3) / 1e9 if relax_ms else 0.0
+    s1, s2 = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 (SSSP), f32 Kahan + f64 residual (PR)",
+        "data": "synthetic", "config": config,
+        "time_to_fixpoint_s": {"sssp": s1["time_ms"] / 1e3, "pagerank": s2["time_ms"] / 1e3},
+        "sweeps": {"sssp": s1["sweeps"], "pagerank": s2["sweeps"]},
+        "graph": {"n": n, "m": E, "struct_bytes": info["struct_bytes"],
+                  "weight_bytes": info["weight_bytes"], "setup_s": setup_s},
+        "e2e": {"value": e2e, "unit": "GTEPS",
+                "h2d_bytes_per_step": streamed // args.steps,
+                "d2h_bytes_per_step": 2 * 4 * n},
+        "roofline": {"bound": "hbm", "kernel": "relax_kernel", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "link_roofline": {"bound": "link", "achieved": streamed / (dev_s * 1e9) if dev_s else 0,
+                          "peak": link, "unit": "GB/s",
+                          "frac": (streamed / (link * 1e9)) / dev_s if dev_s else 0,
+                          "copy_busy_frac": copy_ms / 1e3 / dev_s if dev_s else 0},
+        "relax": {"launches": relax_launches, "ms": relax_ms, "bytes": relax_bytes},
+        "gpu_launches": int(sum(a["kernel_launches"] + b["kernel_launches"] for a, b in stats)),
+        "clocks": clk.summary(),
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        g_s, t_s, desc, thr = cpu_oracle_sample(args.cpu_scale)
+        line["cpu_baseline"] = {"value": g_s, "unit": "GTEPS", "cores": thr, "kind": "oracle",
+                                "sample": desc, "seconds": t_s}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
