@@ -204,6 +204,37 @@ int seraph_params_default(seraph_params* p, int algo);
 int seraph_run(seraph_graph* g, const seraph_params* p, void* out_values, int out_mem,
                seraph_stats* stats);
 
+/*
+ * No-allocation pull fixpoint (the paper has no counterpart).
+ *
+ * For callers that cannot call cudaMalloc: code whose device memory is owned
+ * by a framework's allocator or memory planner, or a latency-critical loop
+ * where cudaMalloc/cudaFree (which synchronise the device and can fail under
+ * memory pressure) are not allowed.  Runs the pull relaxation of seraph_run --
+ * each vertex takes the minimum over its in-edges, one warp per vertex -- to
+ * its fixpoint over a CSC already in device memory, and allocates nothing:
+ * its only scratch is a file-scope device array sized for
+ * SERAPH_NOALLOC_MAX_VERTICES vertices, held by every GPU that loads the
+ * library until the process exits.
+ *
+ * algo: SERAPH_SSSP, SERAPH_BFS or SERAPH_CC.  col_off[n+1] (uint64) and
+ * row[col_off[n]] (source ids, any order within a destination) and w (NULL =
+ * unit weights) are caller-owned device arrays; values[n] receives the
+ * distances / levels / labels (caller-owned device array); passes_out (host,
+ * may be NULL) receives the number of passes.  For CC pass the symmetric
+ * graph.  Errors: SERAPH_EINVAL (n > SERAPH_NOALLOC_MAX_VERTICES, bad algo,
+ * NULL pointers, source >= n), SERAPH_EOVERFLOW, SERAPH_ECUDA.
+ *
+ * The first call on each device resolves the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the scratch array and each clears it on entry, so calls
+ * that overlap on the GPU race: serialise them.
+ */
+#define SERAPH_NOALLOC_MAX_VERTICES (1u << 20)
+int seraph_pull_fixpoint_noalloc(int algo, uint64_t n, const uint64_t* col_off,
+                                 const uint32_t* row, const uint32_t* w, uint32_t source,
+                                 uint32_t* values, uint32_t* passes_out, void* stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* seraph_last_error(void);
 

@@ -33,6 +33,7 @@ PVU_OFF, PVU_STRONG, PVU_WEAK = 0, 1, 2
 PVUS = {"off": PVU_OFF, "strong": PVU_STRONG, "weak": PVU_WEAK}
 SCHED_FIXED, SCHED_LEARNED = 0, 1
 SYMMETRIZE = 1
+NOALLOC_MAX_VERTICES = 1 << 20
 INF = 0xFFFFFFFF
 
 u8, u32, i32, u64, dbl, vp = (ctypes.c_uint8, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64,
@@ -81,6 +82,8 @@ PROTOTYPES = {
     "seraph_params_default": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int]),
     "seraph_run": (ctypes.c_int, [vp, ctypes.POINTER(Params), vp, ctypes.c_int,
                                   ctypes.POINTER(Stats)]),
+    "seraph_pull_fixpoint_noalloc": (ctypes.c_int, [ctypes.c_int, u64, vp, vp, vp, u32, vp, vp,
+                                                    vp]),
     "seraph_last_error": (ctypes.c_char_p, []),
     "seraph_version": (ctypes.c_char_p, []),
 }

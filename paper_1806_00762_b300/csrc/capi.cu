@@ -36,6 +36,10 @@ int guarded(F&& f) {
 
 }  // namespace
 
+namespace seraph {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace seraph
+
 extern "C" {
 
 const char* seraph_last_error(void) { return g_last_error.c_str(); }
