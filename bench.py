@@ -1,10 +1,14 @@
 """Benchmark: time-to-fixpoint and effective GTEPS of the streamed Seraph hot
 path on R-MAT-28 (2^28 vertices, edge factor 16, a,b,c,d = .57,.19,.19,.05),
 512 destination-range pages in pinned host memory, a 16 GB device edge-buffer
-budget, vertex arrays resident in HBM, SSSP (uint32 weights in [1,255], from
-vertex 0) and PageRank (FP32 Kahan sums, FP64 residual, L1 < 1e-7 or 100
-sweeps), predictive vertex updating on (weak state machine), fixed schedule
-with k = 4 local iterations per resident chunk.
+budget, vertex arrays resident in HBM, SSSP (weights in [1,255], from vertex
+0) and PageRank (FP32 Kahan sums, FP64 residual, L1 < 1e-7 or 100 sweeps),
+predictive vertex updating on (strong conditions for SSSP, the weak state
+machine for PageRank), fixed (non-learned) schedules per algorithm.
+
+Besides the timed steps, one run of each algorithm with the paper's plain
+schedule -- a sliding window of k = 4 chunks over a ring of 5 slots, cyclic
+order, weak prediction -- is reported as `paper_schedule` for comparison.
 
 One step = SSSP to its fixpoint + PageRank to its stop rule.  `value` is the
 effective GTEPS of the step (edges of the graph, counted once per algorithm,
@@ -44,9 +48,11 @@ def parse():
     ap.add_argument("--scale", type=int, default=28)
     ap.add_argument("--pages", type=int, default=512)
     ap.add_argument("--budget-gb", type=float, default=16.0)
-    ap.add_argument("--window", type=int, default=4)
-    ap.add_argument("--passes", type=int, default=1)
-    ap.add_argument("--pvu", default="weak")
+    ap.add_argument("--sssp", default="order=cyclic,window=1,slots=16,pvu=strong",
+                    help="SSSP schedule: comma-separated seraph_params overrides")
+    ap.add_argument("--pagerank", default="order=zigzag,window=1,slots=16,pvu=weak",
+                    help="PageRank schedule: comma-separated seraph_params overrides")
+    ap.add_argument("--no-paper-schedule", action="store_true")
     ap.add_argument("--cpu-scale", type=int, default=22, help="R-MAT scale of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -133,17 +139,26 @@ def build_graph(seraph, synth, torch, scale, pages):
     return g
 
 
-def algo_bytes(algo, st) -> float:
+def parse_sched(text: str) -> dict:
+    out = {}
+    for item in filter(None, text.split(",")):
+        k, v = item.split("=")
+        out[k.strip()] = v.strip() if k.strip() in ("order", "pvu") else int(v)
+    return out
+
+
+def algo_bytes(algo, st, weight_width=4, weak=False) -> float:
     """Algorithmic bytes of the relax kernels of a run:
-    SSSP 12 B/edge (column, weight, gathered distance) + 16 B per attempted
-    vertex (list entry, offset, old value) + 4 B per change; PageRank 8 B/edge
-    (column, gathered contribution) + 20 B per attempted vertex (list entry,
-    offset, old value, new value); +2 B per attempted vertex for the weak
-    prediction state."""
+    SSSP (8 + w) B/edge (column, stored weight of w bytes, gathered distance)
+    + 16 B per attempted vertex (list entry, offset pair, old value) + 4 B per
+    change; PageRank 8 B/edge (column, gathered contribution) + 20 B per
+    attempted vertex (list entry, offset pair, old value, new value); +2 B per
+    attempted vertex when the weak prediction state is read and written."""
     E, V, ch = st["edges_relaxed"], st["vertices_attempted"], st["changes"]
+    extra = 2 * V if weak else 0
     if algo == "sssp":
-        return 12 * E + 16 * V + 4 * ch + 2 * V
-    return 8 * E + 20 * V + 2 * V
+        return (8 + weight_width) * E + 16 * V + 4 * ch + extra
+    return 8 * E + 20 * V + extra
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -182,10 +197,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    sched = {"sssp": parse_sched(args.sssp), "pagerank": parse_sched(args.pagerank)}
     config = {"workload": f"rmat{args.scale}-ef16-streamed", "scale": args.scale, "edge_factor": 16,
-              "pages": args.pages, "budget_gb": args.budget_gb, "window": args.window,
-              "passes": args.passes, "pvu": args.pvu, "algorithms": ["sssp", "pagerank"],
-              "schedule": "fixed", "inputs": "pinned host pages streamed each sweep (the method)",
+              "pages": args.pages, "budget_gb": args.budget_gb, "algorithms": ["sssp", "pagerank"],
+              "schedule": {"kind": "fixed", **sched},
+              "inputs": "pinned host pages streamed each sweep (the method)",
               "l2_flush": "inputs larger than L2 (graph >= 2 GB per sweep)",
               "parallelism": f"replicas{world}"}
 
@@ -226,14 +242,12 @@ def main():
     setup_s = time.time() - t_setup
     link = link_gbps(torch)
     budget = int(args.budget_gb * (1 << 30))
-    common = dict(budget_bytes=budget, window=args.window, passes=args.passes, pvu=args.pvu,
-                  profile=1)
     out_u = np.empty(n, dtype=np.uint32)
     out_f = np.empty(n, dtype=np.float32)
 
-    def step():
-        _, s1 = seraph.run(g, "sssp", out=out_u, source=0, **common)
-        _, s2 = seraph.run(g, "pagerank", out=out_f, **common)
+    def step(sssp_kw=sched["sssp"], pr_kw=sched["pagerank"]):
+        _, s1 = seraph.run(g, "sssp", out=out_u, source=0, budget_bytes=budget, profile=1, **sssp_kw)
+        _, s2 = seraph.run(g, "pagerank", out=out_f, budget_bytes=budget, profile=1, **pr_kw)
         return s1, s2
 
     for _ in range(args.warmup):
@@ -260,7 +274,10 @@ def main():
     units = 2 * E * args.steps * world
     value = units / dev_s / 1e9
     e2e = units / wall_calls_s / 1e9
-    relax_bytes = sum(algo_bytes("sssp", s1) + algo_bytes("pagerank", s2) for s1, s2 in stats)
+    ww = info.get("weight_width", 4)
+    relax_bytes = sum(algo_bytes("sssp", s1, ww, sched["sssp"].get("pvu") == "weak") +
+                      algo_bytes("pagerank", s2, ww, sched["pagerank"].get("pvu") == "weak")
+                      for s1, s2 in stats)
     relax_ms = sum(s1["relax_ms"] + s2["relax_ms"] for s1, s2 in stats)
     relax_launches = sum(s1["relax_launches"] + s2["relax_launches"] for s1, s2 in stats)
     streamed = sum(s1["bytes_streamed"] + s2["bytes_streamed"] for s1, s2 in stats)
@@ -297,6 +314,14 @@ def main():
         "clocks": clk.summary(),
         "wall_s_timed": wall,
     }
+    if not args.no_paper_schedule:
+        plain = dict(order="cyclic", window=4, slots=5, pvu="weak")
+        p1, p2 = step(plain, plain)
+        line["paper_schedule"] = {
+            "schedule": plain, "time_to_fixpoint_s": {"sssp": p1["time_ms"] / 1e3,
+                                                       "pagerank": p2["time_ms"] / 1e3},
+            "sweeps": {"sssp": p1["sweeps"], "pagerank": p2["sweeps"]},
+            "gteps": 2 * E / ((p1["time_ms"] + p2["time_ms"]) / 1e3) / 1e9}
     if rank == 0 and not args.no_cpu_baseline:
         g_s, t_s, desc, thr = cpu_oracle_sample(args.cpu_scale)
         line["cpu_baseline"] = {"value": g_s, "unit": "GTEPS", "cores": thr, "kind": "oracle",

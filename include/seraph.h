@@ -57,6 +57,11 @@ enum seraph_mem  { SERAPH_MEM_HOST = 0, SERAPH_MEM_DEVICE = 1 };
 enum seraph_pvu  { SERAPH_PVU_OFF = 0, SERAPH_PVU_STRONG = 1, SERAPH_PVU_WEAK = 2 };
 /* Schedule of the local passes (Sec. 3.2). */
 enum seraph_sched { SERAPH_SCHED_FIXED = 0, SERAPH_SCHED_LEARNED = 1 };
+/* Chunk order across sweeps.  CYCLIC: every sweep streams chunks 0..C-1 and
+ * the window wraps from the last chunk to the first.  ZIGZAG: sweeps
+ * alternate direction, so the window resident at the end of one sweep opens
+ * the next one and is not streamed again (C - window loads per sweep). */
+enum seraph_order { SERAPH_ORDER_CYCLIC = 0, SERAPH_ORDER_ZIGZAG = 1 };
 
 /* Graph flags. */
 #define SERAPH_SYMMETRIZE 1u  /* add (v,u) for every (u,v): the undirected view
@@ -77,6 +82,9 @@ typedef struct seraph_graph_info {
     uint32_t weighted;
     uint32_t symmetrized;
     uint32_t max_in_degree;
+    uint32_t weight_width;      /* bytes per stored weight: 1, 2 or 4 (the
+                                   narrowest that holds the largest weight) */
+    uint32_t reserved;
 } seraph_graph_info;
 
 /*
@@ -88,7 +96,9 @@ typedef struct seraph_graph_info {
  * -- and copy each page into library-owned pinned host memory as
  *   structure: u32 offsets relative to the page (nv+1, padded to 16 B),
  *              u32 source ids (ne, padded to 16 B);
- *   weights:   u32 weights (ne, padded to 16 B), in a separate region so that
+ *   weights:   ne weights of 1, 2 or 4 bytes -- the narrowest width that holds
+ *              the largest weight, a lossless encoding that keeps the streamed
+ *              data compact (padded to 16 B) -- in a separate region so that
  *              unweighted algorithms stream structure only.
  * src/dst/w: m entries each in `mem`; w may be NULL (unweighted).  Every id
  * must be < n (SERAPH_EINVAL otherwise).  Out-degrees are kept resident on the
@@ -121,18 +131,22 @@ void seraph_graph_free(seraph_graph* g);
  * Run parameters.  Fill with seraph_params_default(), then override.
  *
  * Streaming (Sec. 3.2, Fig. 4): the device edge buffer of `budget_bytes` is a
- * ring of window+1 slots.  Pages are packed in order into chunks of at most
- * one slot.  Step t runs `passes` local passes over the `window` most recent
+ * ring of `slots` (default window+1) slots.  Pages are packed in order into
+ * chunks of at most one slot.  Chunks outside the window stay resident as
+ * long as the schedule's look-ahead says they are needed sooner than the
+ * others (furthest-next-use eviction).  Step t runs `passes` local passes over the `window` most recent
  * chunks while the next chunk copies into the free slot, then the oldest chunk
  * leaves the window: with passes = 1 every chunk gets `window` passes per
  * sweep and shares them with its neighbours (the sliding "super subgraph");
  * window = 1, passes = k is the double-buffer variant.  If all chunks fit in
- * the ring at once they are loaded once and never re-streamed.  A sweep is one
- * step per chunk; every chunk is processed `window * passes` times in it.
+ * the ring at once they are loaded once and never re-streamed.  A sweep runs
+ * the window over every chunk once, in the direction given by `order`.
  *
- * Termination: SSSP/BFS/CC stop after a sweep that ran with prediction off
- * and changed no value (the all-pull retrieval of Sec. 4.3); PageRank stops
- * when the FP64 L1 change between two sweep ends is < tol, or at max_sweeps.
+ * Termination: SSSP/BFS/CC stop once every chunk has been processed with
+ * prediction off after the last value change anywhere (the all-pull
+ * retrieval of Sec. 4.3: a prediction-off sweep is run whenever a predicted
+ * sweep changes nothing); PageRank stops when the FP64 L1 change between two
+ * sweep ends is < tol, or at max_sweeps.
  */
 typedef struct seraph_params {
     int32_t  algo;              /* seraph_algo                                */
@@ -161,7 +175,16 @@ typedef struct seraph_params {
     uint32_t timeout_ms;        /* bound on every host wait                   */
     uint32_t profile;           /* 1: time every relax kernel and step with
                                    CUDA events (fills relax_ms, copy_ms, ...) */
-    uint32_t reserved;
+    uint32_t order;             /* seraph_order: chunk order across sweeps     */
+    uint32_t max_passes;        /* idle-slot filling (Sec. 3.2): after `passes`
+                                   passes keep running passes over the window,
+                                   up to this many per step, while the next
+                                   chunk is still in flight and the last pass
+                                   changed something (<= passes: off)          */
+    uint32_t slots;             /* ring slots the budget is split into, >=
+                                   window + 1 (0 = window + 1).  Slots beyond
+                                   the window keep chunks resident across
+                                   sweeps so they are not streamed again      */
     void*    sched_model;       /* seraph_sched_model* for SERAPH_SCHED_LEARNED */
     void*    stream;            /* cudaStream_t for compute, NULL = own       */
     void*    trace;             /* seraph_trace* to fill, or NULL             */

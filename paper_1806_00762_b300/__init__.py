@@ -138,6 +138,8 @@ def run(graph: Graph, algo, out=None, stream=None, **kw):
     for k, v in kw.items():
         if k == "pvu" and isinstance(v, str):
             v = C.PVUS[v]
+        if k == "order" and isinstance(v, str):
+            v = C.ORDERS[v]
         if k == "fsm_next":
             for i, x in enumerate(v):
                 p.fsm_next[i] = int(x)

@@ -32,6 +32,8 @@ MEM_HOST, MEM_DEVICE = 0, 1
 PVU_OFF, PVU_STRONG, PVU_WEAK = 0, 1, 2
 PVUS = {"off": PVU_OFF, "strong": PVU_STRONG, "weak": PVU_WEAK}
 SCHED_FIXED, SCHED_LEARNED = 0, 1
+ORDER_CYCLIC, ORDER_ZIGZAG = 0, 1
+ORDERS = {"cyclic": ORDER_CYCLIC, "zigzag": ORDER_ZIGZAG}
 SYMMETRIZE = 1
 NOALLOC_MAX_VERTICES = 1 << 20
 INF = 0xFFFFFFFF
@@ -44,7 +46,8 @@ class GraphInfo(ctypes.Structure):
     _fields_ = [("n", u64), ("m_raw", u64), ("m", u64), ("struct_bytes", u64),
                 ("weight_bytes", u64), ("max_page_struct_bytes", u64),
                 ("max_page_weight_bytes", u64), ("num_pages", u32), ("weighted", u32),
-                ("symmetrized", u32), ("max_in_degree", u32)]
+                ("symmetrized", u32), ("max_in_degree", u32), ("weight_width", u32),
+                ("reserved", u32)]
 
 
 class Params(ctypes.Structure):
@@ -53,7 +56,8 @@ class Params(ctypes.Structure):
                 ("fsm_skip_mask", u8), ("kahan", u8), ("pad0", u8 * 2), ("max_sweeps", u32),
                 ("damping", dbl), ("tol", dbl), ("pr_fail_eps", dbl),
                 ("pr_pvu_off_below", dbl), ("thread_max_deg", u32), ("warp_max_deg", u32),
-                ("sched", i32), ("timeout_ms", u32), ("profile", u32), ("reserved", u32),
+                ("sched", i32), ("timeout_ms", u32), ("profile", u32), ("order", u32),
+                ("max_passes", u32), ("slots", u32),
                 ("sched_model", vp), ("stream", vp), ("trace", vp)]
 
 

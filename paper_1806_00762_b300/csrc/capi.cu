@@ -103,6 +103,7 @@ int seraph_graph_get_info(const seraph_graph* g, seraph_graph_info* info) {
         info->weighted = g->weighted;
         info->symmetrized = g->symmetrized;
         info->max_in_degree = g->max_in_degree;
+        info->weight_width = g->weighted ? g->wbytes : 0;
         return SERAPH_OK;
     });
 }

@@ -26,18 +26,43 @@ constexpr int kNT = 256;
 constexpr int kCompactRounds = 4;
 constexpr uint32_t kCompactTile = kNT * kCompactRounds;
 
-__device__ __forceinline__ uint4 ld_stream4(const uint32_t* p) {
+// Streaming loads of the resident chunk (read-only while a pass runs; not
+// kept in L1).  Not volatile: the compiler may batch them for more loads in
+// flight.
+__device__ __forceinline__ uint4 ld_stream4(const void* p) {
     uint4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
     return r;
 }
 
-__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
-    uint32_t r;
-    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+__device__ __forceinline__ uint2 ld_stream2(const void* p) {
+    uint2 r;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
     return r;
+}
+
+__device__ __forceinline__ uint32_t ld_stream(const void* p) {
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
+// Four weights of edges idx..idx+3 (idx a multiple of 4) stored WB bytes wide.
+template <int WB>
+__device__ __forceinline__ void ld_weights4(const uint8_t* w, uint32_t idx, uint32_t out[4]) {
+    if (WB == 1) {
+        const uint32_t v = ld_stream(w + idx);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = (v >> (8 * k)) & 0xFFu;
+    } else if (WB == 2) {
+        const uint2 v = ld_stream2(w + 2 * (uint64_t)idx);
+        out[0] = v.x & 0xFFFFu; out[1] = v.x >> 16; out[2] = v.y & 0xFFFFu; out[3] = v.y >> 16;
+    } else {
+        const uint4 v = ld_stream4(w + 4 * (uint64_t)idx);
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    }
 }
 
 __device__ __forceinline__ uint32_t find_page(const uint32_t* vb, uint32_t first, uint32_t end,
@@ -139,51 +164,80 @@ __device__ __forceinline__ void finish_pr(const AlgoArgs& a, uint32_t v, float s
 
 // ------------------------------------------------------------- one vertex
 
-template <int ALGO, bool KAHAN>
+// Gather-and-reduce over edges idx0..idx0+3 and idx1..idx1+3 (both multiples
+// of 4) restricted to [b, e).  All eight column and gathered-value loads are
+// issued before any is used; lanes outside the range gather a valid address
+// (zero padding or a neighbour's column) and drop the value.
+template <int ALGO, bool KAHAN, int WB>
+__device__ __forceinline__ void gather8(const AlgoArgs& a, const PageLoc& loc, uint32_t b,
+                                        uint32_t e, uint32_t idx0, uint32_t idx1, MinAcc& macc,
+                                        SumAcc& sacc) {
+    const bool two = idx1 < e;
+    const uint4 c0 = ld_stream4(loc.col + idx0);
+    const uint4 c1 = two ? ld_stream4(loc.col + idx1) : make_uint4(0, 0, 0, 0);
+    uint32_t w[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    if (ALGO == ALG_SSSP) {
+        ld_weights4<WB>(loc.w, idx0, w);
+        if (two) ld_weights4<WB>(loc.w, idx1, w + 4);
+    }
+    const uint32_t cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    if (ALGO == ALG_PR) {
+        float g[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) g[j] = a.contrib[cc[j]];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t i = (j < 4 ? idx0 : idx1) + (j & 3);
+            if (i >= b && i < e && (j < 4 || two)) sum_add<KAHAN>(sacc, g[j]);
+        }
+    } else {
+        uint32_t g[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) g[j] = a.val[cc[j]];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t i = (j < 4 ? idx0 : idx1) + (j & 3);
+            if (i >= b && i < e && (j < 4 || two)) {
+                const uint32_t du = g[j];
+                if (ALGO == ALG_CC) {
+                    macc.best = min(macc.best, du);
+                } else if (du != SERAPH_INF) {
+                    const uint32_t s = du + (ALGO == ALG_SSSP ? w[j] : 1u);
+                    if (s < du || s == SERAPH_INF) macc.ovf = true;
+                    else macc.best = min(macc.best, s);
+                }
+            }
+        }
+    }
+}
+
+template <int ALGO, bool KAHAN, int WB>
 __device__ __forceinline__ void vertex_thread(const AlgoArgs& a, unsigned long long ent, float base,
                                               Locals& L) {
     const uint32_t v = (uint32_t)ent, p = (uint32_t)(ent >> 32);
     const PageLoc loc = a.loc[p];
     const uint32_t li = v - loc.vb;
     const uint32_t b = loc.off[li], e = loc.off[li + 1];
-    if (ALGO == ALG_PR) {
-        SumAcc acc{0.f, 0.f};
-        for (uint32_t i = b; i < e; ++i) sum_add<KAHAN>(acc, a.contrib[ld_stream(loc.col + i)]);
-        finish_pr(a, v, acc.s - acc.c, base, e - b, L);
-    } else {
-        MinAcc acc{SERAPH_INF, false};
-        for (uint32_t i = b; i < e; ++i)
-            min_edge<ALGO>(acc, ld_stream(loc.col + i), ALGO == ALG_SSSP ? ld_stream(loc.w + i) : 1u,
-                           a.val);
-        finish_min<ALGO>(a, v, acc, e - b, L);
-    }
+    MinAcc macc{SERAPH_INF, false};
+    SumAcc sacc{0.f, 0.f};
+    for (uint32_t idx = b & ~3u; idx < e; idx += 8)
+        gather8<ALGO, KAHAN, WB>(a, loc, b, e, idx, idx + 4, macc, sacc);
+    if (ALGO == ALG_PR) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L);
+    else finish_min<ALGO>(a, v, macc, e - b, L);
 }
 
-// Group of G lanes (G = 32: a warp; the CTA variant reduces across warps).
-// Lane t of the group reads the aligned 16-byte vectors t, t+G, ... of the
-// vertex's column range [b, e), masking elements outside it.
-template <int ALGO, bool KAHAN>
+// Group of G lanes (G = 32: a warp; G = CTA size for hubs).  Lane t reads the
+// aligned 16-byte column vectors t and t+G of every 8G-edge stretch of the
+// vertex's range [b, e).
+template <int ALGO, bool KAHAN, int WB>
 __device__ __forceinline__ void edges_strided(const AlgoArgs& a, const PageLoc& loc, uint32_t b,
                                               uint32_t e, uint32_t t, uint32_t G, MinAcc& macc,
                                               SumAcc& sacc) {
-    for (uint32_t idx = (b & ~3u) + 4 * t; idx < e; idx += 4 * G) {
-        const uint4 c4 = ld_stream4(loc.col + idx);
-        uint4 w4 = make_uint4(1, 1, 1, 1);
-        if (ALGO == ALG_SSSP) w4 = ld_stream4(loc.w + idx);
-        const uint32_t cc[4] = {c4.x, c4.y, c4.z, c4.w};
-        const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t i = idx + j;
-            if (i >= b && i < e) {
-                if (ALGO == ALG_PR) sum_add<KAHAN>(sacc, a.contrib[cc[j]]);
-                else min_edge<ALGO>(macc, cc[j], ww[j], a.val);
-            }
-        }
-    }
+    for (uint32_t idx = (b & ~3u) + 4 * t; idx < e; idx += 8 * G)
+        gather8<ALGO, KAHAN, WB>(a, loc, b, e, idx, idx + 4 * G, macc, sacc);
 }
 
-template <int ALGO, bool KAHAN>
+template <int ALGO, bool KAHAN, int WB>
 __device__ __forceinline__ void vertex_warp(const AlgoArgs& a, unsigned long long ent, float base,
                                             Locals& L) {
     const uint32_t v = (uint32_t)ent, p = (uint32_t)(ent >> 32);
@@ -193,7 +247,7 @@ __device__ __forceinline__ void vertex_warp(const AlgoArgs& a, unsigned long lon
     const uint32_t lane = lane_id();
     MinAcc macc{SERAPH_INF, false};
     SumAcc sacc{0.f, 0.f};
-    edges_strided<ALGO, KAHAN>(a, loc, b, e, lane, 32, macc, sacc);
+    edges_strided<ALGO, KAHAN, WB>(a, loc, b, e, lane, 32, macc, sacc);
     if (ALGO == ALG_PR) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -208,7 +262,7 @@ __device__ __forceinline__ void vertex_warp(const AlgoArgs& a, unsigned long lon
     }
 }
 
-template <int ALGO, bool KAHAN>
+template <int ALGO, bool KAHAN, int WB>
 __device__ __forceinline__ void vertex_cta(const AlgoArgs& a, unsigned long long ent, float base,
                                            Locals& L, float* s_sum, float* s_comp,
                                            unsigned* s_min, unsigned* s_ovf) {
@@ -219,7 +273,7 @@ __device__ __forceinline__ void vertex_cta(const AlgoArgs& a, unsigned long long
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     MinAcc macc{SERAPH_INF, false};
     SumAcc sacc{0.f, 0.f};
-    edges_strided<ALGO, KAHAN>(a, loc, b, e, threadIdx.x, kNT, macc, sacc);
+    edges_strided<ALGO, KAHAN, WB>(a, loc, b, e, threadIdx.x, kNT, macc, sacc);
     if (ALGO == ALG_PR) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -247,7 +301,7 @@ __device__ __forceinline__ void vertex_cta(const AlgoArgs& a, unsigned long long
     __syncthreads();
 }
 
-__device__ __forceinline__ void flush_locals(const AlgoArgs& a, int par, Locals L) {
+__device__ __forceinline__ void flush_locals(const AlgoArgs& a, int par, uint32_t step, Locals L) {
     unsigned ch = __reduce_add_sync(kFull, L.changed);
     unsigned mn = __reduce_min_sync(kFull, L.minv);
     unsigned ov = __reduce_or_sync(kFull, L.ovf);
@@ -259,6 +313,7 @@ __device__ __forceinline__ void flush_locals(const AlgoArgs& a, int par, Locals 
         if (ch) {
             atomicAdd(&rs->pass_changed[par], ch);
             atomicAdd(&rs->cur.changed, (unsigned long long)ch);
+            atomicAdd(&a.step_changed[step & a.step_mask], ch);
         }
         if (mn != SERAPH_INF) atomicMin(&rs->thr_cur, mn);
         if (ov) atomicOr(&rs->cur.overflow, 1u);
@@ -268,23 +323,27 @@ __device__ __forceinline__ void flush_locals(const AlgoArgs& a, int par, Locals 
 
 // ---------------------------------------------------------------- kernels
 
+__global__ void gate_kernel(RunState* rs, uint32_t pass, int check_prev, int idle,
+                            uint32_t want_loaded) {
+    const int par = pass & 1;
+    bool go = true;
+    if (check_prev && rs->pass_changed[par ^ 1] == 0) go = false;
+    if (idle && (int)(*(volatile unsigned*)&rs->loaded - want_loaded) >= 0) go = false;
+    rs->pass_go[par] = go;
+    for (int k = 0; k < 4; ++k) rs->work[par][k] = 0;
+    rs->pass_changed[par] = 0;
+    if (go) rs->cur.passes_run += 1;
+    else rs->cur.passes_skipped += 1;
+}
+
 template <int ALGO>
 __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a, uint32_t pass,
-                                                      int check_prev, int predict) {
+                                                      int predict) {
     __shared__ unsigned ws[kNT / 32 + 1];
     __shared__ unsigned s_base[3];
     const int par = pass & 1;
     RunState* rs = a.rs;
-    if (blockIdx.x == 0) {
-        if (threadIdx.x < 4) rs->work[par][threadIdx.x] = 0;
-        if (threadIdx.x == 4) rs->pass_changed[par] = 0;
-    }
-    const bool skip_pass = check_prev && rs->pass_changed[par ^ 1] == 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (skip_pass) atomicAdd(&rs->cur.passes_skipped, 1u);
-        else atomicAdd(&rs->cur.passes_run, 1u);
-    }
-    if (skip_pass) return;
+    if (!rs->pass_go[par]) return;
 
     int c = 0;
     while (c + 1 < (int)wd.nchunks && blockIdx.x >= wd.c[c + 1].block_begin) ++c;
@@ -308,7 +367,7 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
             const PageLoc loc = a.loc[p];
             const uint32_t li = v - loc.vb;
             const uint32_t deg = loc.off[li + 1] - loc.off[li];
-            if (deg > 0) {
+            if (deg > 0 || ALGO == ALG_PR) {
                 bool skip = false;
                 if (strong) {
                     skip = a.val[v] <= thr;
@@ -352,15 +411,15 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
     }
 }
 
-template <int ALGO, bool KAHAN>
-__global__ void __launch_bounds__(kNT) relax_kernel(AlgoArgs a, uint32_t pass, int check_prev) {
+template <int ALGO, bool KAHAN, int WB>
+__global__ void __launch_bounds__(kNT) relax_kernel(AlgoArgs a, uint32_t pass, uint32_t step) {
     __shared__ unsigned s_item;
     __shared__ float s_sum[kNT / 32], s_comp[kNT / 32];
     __shared__ unsigned s_min[kNT / 32], s_ovf[kNT / 32];
     const int par = pass & 1;
     RunState* rs = a.rs;
     if (blockIdx.x == 0 && threadIdx.x < 4) rs->list_cnt[par ^ 1][threadIdx.x] = 0;
-    if (check_prev && rs->pass_changed[par ^ 1] == 0) return;
+    if (!rs->pass_go[par]) return;
     const unsigned n0 = rs->list_cnt[par][0], n1 = rs->list_cnt[par][1], n2 = rs->list_cnt[par][2];
     const float base = ALGO == ALG_PR ? rs->base : 0.f;
     Locals L{0u, SERAPH_INF, 0u, 0ull};
@@ -371,7 +430,7 @@ __global__ void __launch_bounds__(kNT) relax_kernel(AlgoArgs a, uint32_t pass, i
         const unsigned i = s_item;
         __syncthreads();
         if (i >= n2) break;
-        vertex_cta<ALGO, KAHAN>(a, a.list[2][i], base, L, s_sum, s_comp, s_min, s_ovf);
+        vertex_cta<ALGO, KAHAN, WB>(a, a.list[2][i], base, L, s_sum, s_comp, s_min, s_ovf);
     }
     const unsigned lane = lane_id();
     for (;;) {  // one warp per medium vertex, four at a time
@@ -380,7 +439,7 @@ __global__ void __launch_bounds__(kNT) relax_kernel(AlgoArgs a, uint32_t pass, i
         i0 = __shfl_sync(kFull, i0, 0);
         if (i0 >= n1) break;
         for (unsigned j = 0; j < 4 && i0 + j < n1; ++j)
-            vertex_warp<ALGO, KAHAN>(a, a.list[1][i0 + j], base, L);
+            vertex_warp<ALGO, KAHAN, WB>(a, a.list[1][i0 + j], base, L);
     }
     for (;;) {  // one thread per small vertex, 128 per warp grab
         unsigned i0 = 0;
@@ -390,16 +449,16 @@ __global__ void __launch_bounds__(kNT) relax_kernel(AlgoArgs a, uint32_t pass, i
 #pragma unroll
         for (unsigned j = 0; j < 4; ++j) {
             const unsigned i = i0 + j * 32 + lane;
-            if (i < n0) vertex_thread<ALGO, KAHAN>(a, a.list[0][i], base, L);
+            if (i < n0) vertex_thread<ALGO, KAHAN, WB>(a, a.list[0][i], base, L);
         }
     }
-    flush_locals(a, par, L);
+    flush_locals(a, par, step, L);
 }
 
-__global__ void __launch_bounds__(kNT) pr_apply_kernel(AlgoArgs a, uint32_t pass, int check_prev) {
+__global__ void __launch_bounds__(kNT) pr_apply_kernel(AlgoArgs a, uint32_t pass) {
     const int par = pass & 1;
     RunState* rs = a.rs;
-    if (check_prev && rs->pass_changed[par ^ 1] == 0) return;
+    if (!rs->pass_go[par]) return;
     const unsigned n[3] = {rs->list_cnt[par][0], rs->list_cnt[par][1], rs->list_cnt[par][2]};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (int k = 0; k < 3; ++k) {
@@ -414,14 +473,16 @@ __global__ void __launch_bounds__(kNT) pr_apply_kernel(AlgoArgs a, uint32_t pass
 
 __global__ void set_locs_kernel(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t end,
                                 const uint64_t* rel_soff, const uint64_t* rel_woff,
-                                const uint64_t* off_bytes, uint8_t* sbase, uint8_t* wbase) {
+                                const uint64_t* off_bytes, uint8_t* sbase, uint8_t* wbase,
+                                RunState* rs, uint32_t seq) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile unsigned*)&rs->loaded = seq;
     for (uint32_t p = first + blockIdx.x * blockDim.x + threadIdx.x; p < end;
          p += gridDim.x * blockDim.x) {
         PageLoc L;
         const uint8_t* s = sbase + rel_soff[p];
         L.off = (const uint32_t*)s;
         L.col = (const uint32_t*)(s + off_bytes[p]);
-        L.w = wbase ? (const uint32_t*)(wbase + rel_woff[p]) : nullptr;
+        L.w = wbase ? wbase + rel_woff[p] : nullptr;
         L.vb = vb[p];
         L.nv = vb[p + 1] - vb[p];
         loc[p] = L;
@@ -462,17 +523,28 @@ __global__ void close_min_kernel(RunState* rs, SweepReport* out) {
     rs->cur = SweepReport{};
 }
 
-// PageRank sweep close, step 1: per-block FP64 sums of dangling mass.
-__global__ void __launch_bounds__(kNT) pr_dangling_kernel(const float* x, const float* inv_out,
-                                                          uint64_t n, double* partial) {
+// PageRank sweep close, one pass over the vertices: FP64 partial sums of the
+// dangling mass D = sum of x over out-degree-0 vertices and of the L1 change
+// |x - x_prev| against the last sweep end, then the snapshot x_prev = x.
+// |x - x_prev| in FP32 is exact whenever the two are within a factor of two
+// (Sterbenz), else correctly rounded; the sums are FP64.
+__global__ void __launch_bounds__(kNT) pr_close_partial_kernel(const float* x, float* x_prev,
+                                                               const float* inv_out, uint64_t n,
+                                                               double* part_r, double* part_d) {
     __shared__ double ws[kNT / 32 + 1];
-    double s = 0.0;
+    double r = 0.0, d = 0.0;
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-         v += (uint64_t)gridDim.x * blockDim.x)
-        if (inv_out[v] == 0.0f) s += (double)x[v];
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const float xv = x[v];
+        r += (double)fabsf(xv - x_prev[v]);
+        if (inv_out[v] == 0.0f) d += (double)xv;
+        x_prev[v] = xv;
+    }
     double tot;
-    block_excl_scan<kNT>(s, ws, &tot);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+    block_excl_scan<kNT>(r, ws, &tot);
+    if (threadIdx.x == 0) part_r[blockIdx.x] = tot;
+    block_excl_scan<kNT>(d, ws, &tot);
+    if (threadIdx.x == 0) part_d[blockIdx.x] = tot;
 }
 
 // Fixed-order FP64 reduction of `nparts` partials by one block.
@@ -484,54 +556,29 @@ __device__ double reduce_partials(const double* partial, int nparts, double* ws)
     return tot;
 }
 
-__global__ void __launch_bounds__(kNT) pr_base_kernel(RunState* rs, const double* partial,
-                                                      int nparts, uint64_t n, double d) {
+// Residual and dangling mass of the sweep; base term (1-d)/n + d D/n for the
+// next sweep (the dangling mass lags one sweep, which leaves the fixpoint
+// unchanged).  `out` may be null (initialisation).
+__global__ void __launch_bounds__(kNT) pr_close_final_kernel(RunState* rs, const double* part_r,
+                                                             const double* part_d, int nparts,
+                                                             uint64_t n, double damping,
+                                                             SweepReport* out) {
     __shared__ double ws[kNT / 32 + 1];
-    double D = reduce_partials(partial, nparts, ws);
-    if (threadIdx.x == 0) {
-        rs->dsum = D;
-        rs->base = (float)((1.0 - d) / (double)n + d * D / (double)n);
-    }
-}
-
-// Step 2: zero-in-degree vertices take the new base value (their whole
-// PageRank equation), then the FP64 L1 change against the last sweep end.
-__global__ void __launch_bounds__(kNT) pr_resid_kernel(RunState* rs, float* x, float* contrib,
-                                                       const float* inv_out, float* x_prev,
-                                                       const uint32_t* zero_in, uint64_t n,
-                                                       double* partial) {
-    __shared__ double ws[kNT / 32 + 1];
-    const float base = rs->base;
-    double s = 0.0;
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-         v += (uint64_t)gridDim.x * blockDim.x) {
-        float xv = x[v];
-        if ((zero_in[v >> 5] >> (v & 31)) & 1u) {
-            xv = base;
-            x[v] = xv;
-            contrib[v] = xv * inv_out[v];
-        }
-        s += fabs((double)xv - (double)x_prev[v]);
-        x_prev[v] = xv;
-    }
-    double tot;
-    block_excl_scan<kNT>(s, ws, &tot);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kNT) pr_close_kernel(RunState* rs, const double* partial,
-                                                       int nparts, SweepReport* out) {
-    __shared__ double ws[kNT / 32 + 1];
-    double r = reduce_partials(partial, nparts, ws);
+    const double r = reduce_partials(part_r, nparts, ws);
+    const double D = reduce_partials(part_d, nparts, ws);
     if (threadIdx.x == 0) {
         rs->rsum = r;
-        SweepReport rep = rs->cur;
-        rep.resid = r;
-        rep.dangling = rs->dsum;
-        rep.thr_min = rs->thr_cur;
-        *out = rep;
-        rs->sweeps_done += 1;
-        rs->cur = SweepReport{};
+        rs->dsum = D;
+        rs->base = (float)((1.0 - damping) / (double)n + damping * D / (double)n);
+        if (out) {
+            SweepReport rep = rs->cur;
+            rep.resid = r;
+            rep.dangling = D;
+            rep.thr_min = rs->thr_cur;
+            *out = rep;
+            rs->sweeps_done += 1;
+            rs->cur = SweepReport{};
+        }
     }
 }
 
@@ -542,43 +589,53 @@ unsigned grid_1d(uint64_t n) {
 
 }  // namespace
 
+void launch_gate(RunState* rs, uint32_t pass, int check_prev, int idle, uint32_t want_loaded,
+                 cudaStream_t s) {
+    gate_kernel<<<1, 1, 0, s>>>(rs, pass, check_prev, idle, want_loaded);
+    SR_LAUNCH();
+}
+
 void launch_compact(int algo, const WindowDesc& wd, const AlgoArgs& a, uint32_t pass,
-                    int check_prev, int predict, cudaStream_t s) {
+                    int predict, cudaStream_t s) {
     const unsigned g = wd.nblocks ? wd.nblocks : 1;
     switch (algo) {
-        case ALG_SSSP: compact_kernel<ALG_SSSP><<<g, kNT, 0, s>>>(wd, a, pass, check_prev, predict); break;
-        case ALG_BFS: compact_kernel<ALG_BFS><<<g, kNT, 0, s>>>(wd, a, pass, check_prev, predict); break;
-        case ALG_CC: compact_kernel<ALG_CC><<<g, kNT, 0, s>>>(wd, a, pass, check_prev, predict); break;
-        default: compact_kernel<ALG_PR><<<g, kNT, 0, s>>>(wd, a, pass, check_prev, predict); break;
+        case ALG_SSSP: compact_kernel<ALG_SSSP><<<g, kNT, 0, s>>>(wd, a, pass, predict); break;
+        case ALG_BFS: compact_kernel<ALG_BFS><<<g, kNT, 0, s>>>(wd, a, pass, predict); break;
+        case ALG_CC: compact_kernel<ALG_CC><<<g, kNT, 0, s>>>(wd, a, pass, predict); break;
+        default: compact_kernel<ALG_PR><<<g, kNT, 0, s>>>(wd, a, pass, predict); break;
     }
     SR_LAUNCH();
 }
 
-void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, int check_prev, int grid,
+void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, uint32_t step, int grid,
                   cudaStream_t s) {
     switch (algo) {
-        case ALG_SSSP: relax_kernel<ALG_SSSP, false><<<grid, kNT, 0, s>>>(a, pass, check_prev); break;
-        case ALG_BFS: relax_kernel<ALG_BFS, false><<<grid, kNT, 0, s>>>(a, pass, check_prev); break;
-        case ALG_CC: relax_kernel<ALG_CC, false><<<grid, kNT, 0, s>>>(a, pass, check_prev); break;
+        case ALG_SSSP:
+            if (a.wbytes == 1) relax_kernel<ALG_SSSP, false, 1><<<grid, kNT, 0, s>>>(a, pass, step);
+            else if (a.wbytes == 2) relax_kernel<ALG_SSSP, false, 2><<<grid, kNT, 0, s>>>(a, pass, step);
+            else relax_kernel<ALG_SSSP, false, 4><<<grid, kNT, 0, s>>>(a, pass, step);
+            break;
+        case ALG_BFS: relax_kernel<ALG_BFS, false, 4><<<grid, kNT, 0, s>>>(a, pass, step); break;
+        case ALG_CC: relax_kernel<ALG_CC, false, 4><<<grid, kNT, 0, s>>>(a, pass, step); break;
         default:
-            if (kahan) relax_kernel<ALG_PR, true><<<grid, kNT, 0, s>>>(a, pass, check_prev);
-            else relax_kernel<ALG_PR, false><<<grid, kNT, 0, s>>>(a, pass, check_prev);
+            if (kahan) relax_kernel<ALG_PR, true, 4><<<grid, kNT, 0, s>>>(a, pass, step);
+            else relax_kernel<ALG_PR, false, 4><<<grid, kNT, 0, s>>>(a, pass, step);
             break;
     }
     SR_LAUNCH();
 }
 
-void launch_pr_apply(const AlgoArgs& a, uint32_t pass, int check_prev, int grid, cudaStream_t s) {
-    pr_apply_kernel<<<grid, kNT, 0, s>>>(a, pass, check_prev);
+void launch_pr_apply(const AlgoArgs& a, uint32_t pass, int grid, cudaStream_t s) {
+    pr_apply_kernel<<<grid, kNT, 0, s>>>(a, pass);
     SR_LAUNCH();
 }
 
 void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t end,
                      const uint64_t* rel_soff, const uint64_t* rel_woff, const uint64_t* off_bytes,
-                     uint8_t* sbase, uint8_t* wbase, cudaStream_t s) {
-    if (end <= first) return;
-    unsigned g = (end - first + kNT - 1) / kNT;
-    set_locs_kernel<<<g, kNT, 0, s>>>(loc, vb, first, end, rel_soff, rel_woff, off_bytes, sbase, wbase);
+                     uint8_t* sbase, uint8_t* wbase, RunState* rs, uint32_t seq, cudaStream_t s) {
+    unsigned g = end > first ? (end - first + kNT - 1) / kNT : 1;
+    set_locs_kernel<<<g, kNT, 0, s>>>(loc, vb, first, end, rel_soff, rel_woff, off_bytes, sbase,
+                                       wbase, rs, seq);
     SR_LAUNCH();
 }
 
@@ -600,14 +657,12 @@ void launch_close_min(RunState* rs, SweepReport* out, cudaStream_t s) {
     SR_LAUNCH();
 }
 
-void launch_close_pr(const AlgoArgs& a, uint64_t n, float* x_prev, const uint32_t* zero_in,
-                     double damping, double* partial, int nparts, SweepReport* out,
-                     cudaStream_t s) {
-    pr_dangling_kernel<<<nparts, kNT, 0, s>>>(a.x, a.inv_out, n, partial);
-    pr_base_kernel<<<1, kNT, 0, s>>>(a.rs, partial, nparts, n, damping);
-    pr_resid_kernel<<<nparts, kNT, 0, s>>>(a.rs, a.x, a.contrib, a.inv_out, x_prev, zero_in, n,
-                                            partial);
-    if (out) pr_close_kernel<<<1, kNT, 0, s>>>(a.rs, partial, nparts, out);
+void launch_close_pr(const AlgoArgs& a, uint64_t n, float* x_prev, double damping,
+                     double* partial, int nparts, SweepReport* out, cudaStream_t s) {
+    pr_close_partial_kernel<<<nparts, kNT, 0, s>>>(a.x, x_prev, a.inv_out, n, partial,
+                                                    partial + nparts);
+    pr_close_final_kernel<<<1, kNT, 0, s>>>(a.rs, partial, partial + nparts, nparts, n, damping,
+                                             out);
     SR_LAUNCH();
 }
 

@@ -14,7 +14,7 @@ constexpr int kMaxWindow = 16;
 struct PageLoc {
     const uint32_t* off;  // nv+1 page-relative offsets
     const uint32_t* col;  // ne source ids (16-byte aligned)
-    const uint32_t* w;    // ne weights (16-byte aligned) or null
+    const uint8_t* w;     // ne weights, wbytes each (16-byte aligned) or null
     uint32_t vb;          // first vertex
     uint32_t nv;          // vertices
 };
@@ -41,6 +41,9 @@ struct SweepReport {
 
 struct RunState {
     SweepReport cur;
+    unsigned int pass_go[2];      // pass decision of the gate kernel
+    unsigned int loaded;          // sequence number of the last chunk load done
+    unsigned int pad1;
     unsigned int pass_changed[2];
     unsigned int list_cnt[2][4];
     unsigned int work[2][4];
@@ -62,33 +65,40 @@ struct AlgoArgs {
     const PageLoc* loc;       // per page
     const uint32_t* vb;       // page boundaries (P+1)
     unsigned long long* list[3];  // entries (page << 32) | v, per mapping class
+    unsigned int* step_changed;   // value changes per pipeline step (ring)
+    uint32_t step_mask;           // ring size - 1
     uint32_t thread_max, warp_max;
     float damping, fail_eps;
     uint8_t fsm_next[12];
     uint8_t skip_mask;
     uint8_t pvu;              // SERAPH_PVU_*
-    uint8_t pad[2];
+    uint8_t wbytes;           // stored weight width: 1, 2 or 4 bytes
+    uint8_t pad;
 };
 
 // Launchers (engine.cu).  `pass` is the global pass counter (its parity picks
-// the double-buffered counters); `check_prev` lets the pass exit early on the
-// device when the previous pass of the same step changed nothing;
+// the double-buffered counters).  Every pass starts with a one-thread gate
+// that decides on the device whether the pass runs: it is skipped when
+// `check_prev` is set and the previous pass of the step changed nothing, or
+// when `idle` is set and load number `want_loaded` has already landed (an
+// idle-slot pass is only worth running while the copy is in flight).
 // `predict` = 0 runs the pass with prediction off.
+void launch_gate(RunState* rs, uint32_t pass, int check_prev, int idle, uint32_t want_loaded,
+                 cudaStream_t s);
 void launch_compact(int algo, const WindowDesc& wd, const AlgoArgs& a, uint32_t pass,
-                    int check_prev, int predict, cudaStream_t s);
-void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, int check_prev,
+                    int predict, cudaStream_t s);
+void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, uint32_t step,
                   int grid, cudaStream_t s);
-void launch_pr_apply(const AlgoArgs& a, uint32_t pass, int check_prev, int grid, cudaStream_t s);
+void launch_pr_apply(const AlgoArgs& a, uint32_t pass, int grid, cudaStream_t s);
 void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t end,
                      const uint64_t* rel_soff, const uint64_t* rel_woff, const uint64_t* off_bytes,
-                     uint8_t* sbase, uint8_t* wbase, cudaStream_t s);
+                     uint8_t* sbase, uint8_t* wbase, RunState* rs, uint32_t seq, cudaStream_t s);
 void launch_init_values(int algo, const AlgoArgs& a, uint64_t n, uint32_t source,
                         cudaStream_t s);
 void launch_init_pr(const uint32_t* outdeg, const AlgoArgs& a, float* x_prev, uint64_t n,
                     cudaStream_t s);
 void launch_close_min(RunState* rs, SweepReport* out, cudaStream_t s);
-void launch_close_pr(const AlgoArgs& a, uint64_t n, float* x_prev, const uint32_t* zero_in,
-                     double damping, double* partial, int nparts, SweepReport* out,
-                     cudaStream_t s);
+void launch_close_pr(const AlgoArgs& a, uint64_t n, float* x_prev, double damping,
+                     double* partial, int nparts, SweepReport* out, cudaStream_t s);
 
 }  // namespace seraph

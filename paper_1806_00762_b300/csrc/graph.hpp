@@ -20,7 +20,7 @@ struct PageMeta {
     uint64_t s_bytes;   // structure bytes (offsets + columns, padded)
     uint64_t off_bytes; // bytes of the padded offset array
     uint64_t w_off;     // byte offset in the weight region
-    uint64_t w_bytes;   // weight bytes (padded), 0 if unweighted
+    uint64_t w_bytes;   // weight bytes (ne * weight width, padded), 0 if unweighted
 };
 
 struct seraph_graph {
@@ -29,6 +29,7 @@ struct seraph_graph {
     uint32_t num_pages = 0;
     bool weighted = false, symmetrized = false;
     uint32_t max_in_degree = 0;
+    uint32_t wbytes = 4;               // stored weight width (1, 2 or 4 bytes)
     std::vector<PageMeta> pages;
     std::vector<uint64_t> vb;          // num_pages + 1 page boundaries
     seraph::PinnedBuf h_struct;        // all page structures, in page order

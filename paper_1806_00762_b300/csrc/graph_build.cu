@@ -328,6 +328,25 @@ __global__ void max_indeg_kernel(const uint64_t* __restrict__ col_off, uint64_t 
     if (lane_id() == 0) atomicMax(mx, local);
 }
 
+__global__ void max_u32_kernel(const uint32_t* __restrict__ a, uint64_t n, unsigned* mx) {
+    unsigned local = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        local = max(local, a[i]);
+    local = __reduce_max_sync(kFull, local);
+    if (lane_id() == 0) atomicMax(mx, local);
+}
+
+// Weights narrowed to `wb` bytes (lossless: wb is chosen from the maximum).
+__global__ void narrow_kernel(const uint32_t* __restrict__ w, uint64_t n, int wb,
+                              uint8_t* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (wb == 1) out[i] = (uint8_t)w[i];
+        else ((uint16_t*)out)[i] = (uint16_t)w[i];
+    }
+}
+
 __global__ void zero_in_kernel(const uint64_t* __restrict__ col_off, uint64_t n,
                                uint32_t* __restrict__ bits) {
     const uint64_t words = (n + 31) / 32;
@@ -495,6 +514,27 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     keys.release();
     vals.release();
     g->m = E;
+    // Narrowest lossless weight width (Sec. 3.1: the page format keeps the
+    // transferred data as compact as possible).
+    DevBuf<uint8_t> wnar;
+    if (weighted && E) {
+        DevBuf<unsigned> mx(1);
+        SR_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned), s));
+        max_u32_kernel<<<grid_for(E), kNT, 0, s>>>(wcol.p, E, mx.p);
+        SR_LAUNCH();
+        unsigned hmx = 0;
+        SR_CUDA(cudaMemcpyAsync(&hmx, mx.p, 4, cudaMemcpyDeviceToHost, s));
+        SR_CUDA(cudaStreamSynchronize(s));
+        g->wbytes = hmx <= 0xFFu ? 1 : (hmx <= 0xFFFFu ? 2 : 4);
+        if (g->wbytes < 4) {
+            wnar.alloc(E * g->wbytes);
+            narrow_kernel<<<grid_for(E), kNT, 0, s>>>(wcol.p, E, (int)g->wbytes, wnar.p);
+            SR_LAUNCH();
+            SR_CUDA(cudaStreamSynchronize(s));
+            wcol.release();
+        }
+    }
+    const uint8_t* wsrc = g->wbytes < 4 ? wnar.p : (const uint8_t*)wcol.p;
 
     DevBuf<uint64_t> col_off(n + 1);
     col_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(dcol.p, E, n, col_off.p);
@@ -540,7 +580,7 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
         SR_CHECK(pm.ne < 0xFFFFFFFFull, SERAPH_EOVERFLOW, "a page holds 2^32 or more edges");
         pm.off_bytes = align_up(4 * (pm.nv + 1), 16);
         pm.s_bytes = pm.off_bytes + align_up(4 * pm.ne, 16);
-        pm.w_bytes = weighted ? align_up(4 * pm.ne, 16) : 0;
+        pm.w_bytes = weighted ? align_up((uint64_t)g->wbytes * pm.ne, 16) : 0;
         pm.s_off = s_off;
         pm.w_off = w_off;
         s_off += pm.s_bytes;
@@ -576,9 +616,11 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
         std::memset(hs + pm.off_bytes + 4 * pm.ne, 0, pm.s_bytes - pm.off_bytes - 4 * pm.ne);
         if (weighted) {
             uint8_t* hw = g->h_weight.p + pm.w_off;
+            const uint64_t nb = (uint64_t)g->wbytes * pm.ne;
             if (pm.ne)
-                SR_CUDA(cudaMemcpyAsync(hw, wcol.p + pm.e0, 4 * pm.ne, cudaMemcpyDeviceToHost, s));
-            std::memset(hw + 4 * pm.ne, 0, pm.w_bytes - 4 * pm.ne);
+                SR_CUDA(cudaMemcpyAsync(hw, wsrc + (uint64_t)g->wbytes * pm.e0, nb,
+                                        cudaMemcpyDeviceToHost, s));
+            std::memset(hw + nb, 0, pm.w_bytes - nb);
         }
     }
     SR_CUDA(cudaStreamSynchronize(s));
@@ -618,8 +660,14 @@ void export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* row, uint32_
         if (col_off)
             for (uint64_t i = 0; i < pm.nv; ++i) col_off[pm.vb + i] = pm.e0 + off[i];
         if (row && pm.ne) std::memcpy(row + pm.e0, c, 4 * pm.ne);
-        if (w && g->weighted && pm.ne)
-            std::memcpy(w + pm.e0, g->h_weight.p + pm.w_off, 4 * pm.ne);
+        if (w && g->weighted && pm.ne) {
+            const uint8_t* hw = g->h_weight.p + pm.w_off;
+            for (uint64_t i = 0; i < pm.ne; ++i) {
+                uint32_t x = 0;
+                std::memcpy(&x, hw + i * g->wbytes, g->wbytes);  // little-endian widths
+                w[pm.e0 + i] = x;
+            }
+        }
     }
     if (col_off) col_off[g->n] = g->m;
     if (out_degree) {

@@ -1,16 +1,26 @@
 // Host sweep driver: pipelined subgraph iteration (Sec. 3.2, Fig. 4) with
 // predictive vertex updating (Sec. 4) to a fixpoint.
 //
-// The device edge buffer is a ring of window+1 slots.  Global step t
-//   (1) enqueues, on the copy stream, the host->device copy of the chunk of
-//       step t+1 into slot (t+1) mod R, after the event of step t-1 (the last
-//       step whose window held that slot's previous chunk);
+// The device edge buffer is a ring of `slots` (>= window+1) slots.  Every
+// pipeline step
+//   (1) enqueues, on the copy stream, the host->device copy of the chunk the
+//       next step needs into the free slot, after the event of the step that
+//       last used that slot;
 //   (2) enqueues, on the compute stream, `passes` local passes over the
-//       window (chunks t-window+1 .. t) once the copy of chunk t is done.
-// A sweep is C consecutive steps (C = chunks); every chunk gets
-// window * passes passes in it.  At the end of a sweep one small report is
-// copied back; the host reads it while the next chunk is already in flight
-// and decides: continue, run a prediction-off verification sweep, or stop.
+//       window of resident chunks once their copies are done, then up to
+//       `max_passes` idle-slot passes that each run only while the copy of
+//       (1) is still in flight and the previous pass changed something;
+//   (3) evicts one chunk of the window; its slot becomes the next free slot.
+// Which chunk comes next is the schedule's choice: the paper's sliding
+// window wraps cyclically; the zigzag order reverses at each end so that the
+// resident window opens the next sweep without being streamed again.
+//
+// Per-step change counts live on the device.  At the end of a sweep one
+// small report and the step counts are copied back while the next chunk is
+// already in flight, and the host decides: continue, turn prediction off, or
+// stop.  SSSP/BFS/CC stop once every chunk has been processed with
+// prediction off after the last change anywhere; PageRank stops on the FP64
+// L1 change between sweep ends.
 #include <chrono>
 #include <cstring>
 #include <thread>
@@ -56,6 +66,60 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
+// Window schedules over C chunks with a window of W.  window(t) is the set of
+// chunks step t processes; it is a pure function of t (a ramp followed by a
+// periodic part, both tabulated once) so that the driver can look ahead for
+// loads and evictions.
+class Schedule {
+  public:
+    Schedule(uint32_t C, uint32_t W, int order, bool resident)
+        : C_(C), W_(resident ? (W < C ? W : C) : W), zigzag_(!resident && order == SERAPH_ORDER_ZIGZAG) {
+        if (!zigzag_) {  // sliding window, cyclic over the chunks
+            ramp_ = W_ - 1;
+            period_ = C_;
+            for (uint64_t t = 0; t < ramp_ + period_; ++t) {
+                const uint64_t wn = std::min<uint64_t>(W_, t + 1);
+                const uint32_t c = (uint32_t)(t % C_);
+                std::vector<uint32_t> w;
+                for (uint64_t k = 0; k < wn; ++k) w.push_back((uint32_t)((c + C_ - (wn - 1 - k)) % C_));
+                table_.push_back(w);
+            }
+        } else {  // lowest chunk: 0,1,..,C-W (forward), C-W-1,..,1 (back)
+            ramp_ = W_ - 1;
+            const uint64_t span = C_ - W_;
+            period_ = 2 * span;
+            for (uint64_t t = 0; t < ramp_; ++t) {
+                std::vector<uint32_t> w;
+                for (uint32_t k = 0; k <= t; ++k) w.push_back(k);
+                table_.push_back(w);
+            }
+            for (uint64_t u = 0; u < period_; ++u) {
+                const uint32_t lo = (uint32_t)(u <= span ? u : 2 * span - u);
+                std::vector<uint32_t> w;
+                for (uint32_t k = 0; k < W_; ++k) w.push_back(lo + k);
+                table_.push_back(w);
+            }
+        }
+    }
+
+    const std::vector<uint32_t>& window(uint64_t t) const {
+        return table_[t < ramp_ ? t : ramp_ + (t - ramp_) % period_];
+    }
+
+    bool sweep_end(uint64_t t) const {
+        if (!zigzag_) return t % C_ == C_ - 1;
+        if (t < ramp_) return false;
+        const uint64_t u = t - ramp_, span = C_ - W_;
+        return u > 0 && u % span == 0;
+    }
+
+  private:
+    uint32_t C_, W_;
+    bool zigzag_;
+    uint64_t ramp_ = 0, period_ = 1;
+    std::vector<std::vector<uint32_t>> table_;
+};
+
 }  // namespace
 
 int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, seraph_stats* st) {
@@ -64,6 +128,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CHECK(P->algo >= SERAPH_SSSP && P->algo <= SERAPH_PAGERANK, SERAPH_EINVAL, "bad algo");
     SR_CHECK(P->window >= 1 && P->window <= kMaxWindow, SERAPH_EINVAL, "window must be in [1,16]");
     SR_CHECK(P->passes >= 1 && P->passes <= 64, SERAPH_EINVAL, "passes must be in [1,64]");
+    SR_CHECK(P->max_passes <= 64, SERAPH_EINVAL, "max_passes must be <= 64");
+    SR_CHECK(P->order == SERAPH_ORDER_CYCLIC || P->order == SERAPH_ORDER_ZIGZAG, SERAPH_EINVAL,
+             "bad order");
     SR_CHECK(P->pvu >= SERAPH_PVU_OFF && P->pvu <= SERAPH_PVU_WEAK, SERAPH_EINVAL, "bad pvu");
     SR_CHECK(!(P->algo == SERAPH_PAGERANK && P->pvu == SERAPH_PVU_STRONG), SERAPH_EINVAL,
              "PageRank has no strong prediction condition; use weak or off");
@@ -85,7 +152,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
 
     // ------------------------------------------------------------ chunking
     const uint32_t W = P->window;
-    const uint32_t R = W + 1;
+    const uint32_t R = P->slots ? P->slots : W + 1;
+    SR_CHECK(R >= W + 1 && R <= 4096, SERAPH_EINVAL, "slots must be in [window+1, 4096]");
     const uint64_t slot_bytes = (P->budget_bytes / R) & ~255ull;
     SR_CHECK(slot_bytes >= 256, SERAPH_EBUDGET, "budget too small for the ring");
     std::vector<Chunk> chunks;
@@ -118,7 +186,6 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     const uint32_t Weff = W < C ? W : C;
     const uint32_t nslots = resident ? C : R;
 
-    // static per-page placement relative to the chunk image
     std::vector<uint64_t> rel_soff(g->num_pages), rel_woff(g->num_pages), offb(g->num_pages);
     for (const Chunk& c : chunks)
         for (uint32_t p = c.first_page; p < c.end_page; ++p) {
@@ -126,15 +193,18 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             rel_woff[p] = c.w_slot_off + (g->pages[p].w_off - c.w_begin);
             offb[p] = g->pages[p].off_bytes;
         }
+    // list capacity: the most vertices any W consecutive chunks hold
     uint64_t max_win_v = 1;
     for (uint32_t t = 0; t < C; ++t) {
         uint64_t s = 0;
         for (uint32_t k = 0; k < Weff; ++k) {
-            const Chunk& c = chunks[(t + C - k) % C];
+            const Chunk& c = chunks[(t + k) % C];
             s += c.v_end - c.v_begin;
         }
         max_win_v = std::max<uint64_t>(max_win_v, s);
     }
+    uint32_t ring = 1024;
+    while (ring < 4 * (uint64_t)C + 8) ring <<= 1;
 
     // --------------------------------------------------------- allocations
     Stream cs, xs;
@@ -149,8 +219,11 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     DevBuf<unsigned long long> lists(3 * max_win_v);
     DevBuf<RunState> rs(1);
     DevBuf<SweepReport> d_rep(1);
-    PinnedBuf h_rep;
+    DevBuf<unsigned> d_steps(ring);
+    SR_CUDA(cudaMemsetAsync(d_steps.p, 0, ring * sizeof(unsigned), cs.s));
+    PinnedBuf h_rep, h_steps;
     h_rep.alloc(sizeof(SweepReport));
+    h_steps.alloc(ring * sizeof(unsigned));
     DevBuf<uint32_t> val;
     DevBuf<float> x, contrib, x_next, x_prev, inv_out;
     DevBuf<uint8_t> state;
@@ -158,7 +231,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     DevBuf<double> partial;
     if (is_pr) {
         x.alloc(n); contrib.alloc(n); x_next.alloc(n); x_prev.alloc(n); inv_out.alloc(n);
-        partial.alloc(nparts);
+        partial.alloc(2 * nparts);
     } else {
         val.alloc(n);
     }
@@ -175,6 +248,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     a.loc = loc.p;
     a.vb = g->d_vb.p;
     for (int k = 0; k < 3; ++k) a.list[k] = lists.p + k * max_win_v;
+    a.step_changed = d_steps.p;
+    a.step_mask = ring - 1;
     a.thread_max = P->thread_max_deg;
     a.warp_max = P->warp_max_deg;
     a.damping = (float)P->damping;
@@ -182,6 +257,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     std::memcpy(a.fsm_next, P->fsm_next, 12);
     a.skip_mask = P->fsm_skip_mask;
     a.pvu = (uint8_t)P->pvu;
+    a.wbytes = (uint8_t)g->wbytes;
 
     uint64_t launches = 0;
     {
@@ -191,11 +267,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         SR_CUDA(cudaMemcpyAsync(rs.p, &init, sizeof(init), cudaMemcpyHostToDevice, cs.s));
         if (is_pr) {
             launch_init_pr(g->d_outdeg.p, a, x_prev.p, n, cs.s);
-            launch_close_pr(a, n, x_prev.p, g->d_zero_in.p, P->damping, partial.p, nparts,
-                            nullptr, cs.s);
-            launches += 4;
-            // the init residual pass must not count as a sweep
-            SR_CUDA(cudaMemcpyAsync(&rs.p->cur, &init.cur, sizeof(init.cur), cudaMemcpyHostToDevice, cs.s));
+            launch_close_pr(a, n, x_prev.p, P->damping, partial.p, nparts, nullptr, cs.s);
+            launches += 3;
         } else {
             launch_init_values(algo, a, n, P->source, cs.s);
             launches += 1;
@@ -204,22 +277,25 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     }
 
     // -------------------------------------------------------------- events
-    std::vector<Event> copy_done(R), step_done(R);
-    for (uint32_t i = 0; i < R; ++i) { copy_done[i].create(false); step_done[i].create(false); }
+    std::vector<Event> step_done(ring), copy_done(C);
+    std::vector<uint32_t> npass_of(ring, 0);
+    for (auto& e : step_done) e.create(false);
+    for (auto& e : copy_done) e.create(false);
     Event ev_start, ev_stop, ev_sweep;
     ev_start.create(true);
     ev_stop.create(true);
     ev_sweep.create(false);
     const bool prof = P->profile != 0;
-    // per-sweep profiling pools, double-buffered by sweep parity
+    const uint32_t max_passes = std::max(P->max_passes, P->passes);
+    // profiling pools, indexed by step within the ring
     std::vector<Event> pc_b, pc_e, pk_b, pk_e, pr_b, pr_e;
     if (prof) {
         for (auto* v : {&pc_b, &pc_e, &pk_b, &pk_e}) {
-            v->resize(2 * C);
+            v->resize(ring);
             for (auto& e : *v) e.create(true);
         }
         for (auto* v : {&pr_b, &pr_e}) {
-            v->resize(C * P->passes);
+            v->resize((size_t)ring * max_passes);
             for (auto& e : *v) e.create(true);
         }
     }
@@ -227,27 +303,104 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     seraph_stats S{};
     S.chunks = C;
     S.resident = resident;
-    std::vector<uint8_t> loaded(C, 0);
 
-    auto load = [&](uint64_t t) {  // chunk for step t into its slot
-        const uint32_t c = (uint32_t)(t % C);
-        const uint32_t slot = resident ? c : (uint32_t)(t % R);
-        if (!resident && t >= R) SR_CUDA(cudaStreamWaitEvent(xs.s, step_done[(t - 2) % R].e, 0));
+    std::vector<int64_t> slot_of(C, -1);        // chunk -> slot
+    std::vector<int64_t> chunk_in(nslots, -1);   // slot -> chunk
+    std::vector<int64_t> last_use(nslots, -1);   // slot -> last step that used it
+    std::vector<uint8_t> pending(C, 0);          // copied but not yet waited on by compute
+    uint32_t load_seq = 0, loads_timed = 0;
+    Schedule sched(C, W, (int)P->order, resident);
+    const bool zig = !resident && P->order == SERAPH_ORDER_ZIGZAG;
+
+    // Look-ahead over the deterministic window sequence: next step >= from
+    // whose window holds chunk c (or `horizon` if none within it).
+    const uint64_t horizon_len = 2 * (uint64_t)C + 2;
+    auto next_use = [&](uint32_t c, uint64_t from, uint64_t horizon) -> uint64_t {
+        for (uint64_t u = from; u < horizon; ++u)
+            for (uint32_t x : sched.window(u))
+                if (x == c) return u;
+        return horizon;
+    };
+
+    // Eviction choices.  Steps <= t are enqueued; steps > t are not.
+    //  - demand (chunk needed by step t itself): an empty slot, else the
+    //    resident chunk outside window t with the furthest next use;
+    //  - cyclic prefetch for step t+1: the chunk outside windows t and t+1
+    //    with the furthest next use (the classic ring: the chunk that just
+    //    left the window);
+    //  - zigzag prefetch for a later step u: exactly the chunk furthest-next-
+    //    use eviction would pick when step u arrives, and only if no step in
+    //    [t, u) still needs it (otherwise stop prefetching for now).
+    auto take = [&](int64_t s) {
+        slot_of[chunk_in[s]] = -1;
+        chunk_in[s] = -1;
+        return s;
+    };
+    auto empty_slot = [&]() -> int64_t {
+        for (uint32_t s = 0; s < nslots; ++s)
+            if (chunk_in[s] < 0) return s;
+        return -1;
+    };
+    auto slot_demand = [&](uint64_t t) -> int64_t {
+        const int64_t e = empty_slot();
+        if (e >= 0) return e;
+        const std::vector<uint32_t>& win_t = sched.window(t);
+        int64_t best = -1;
+        uint64_t best_next = 0;
+        for (uint32_t s = 0; s < nslots; ++s) {
+            bool in_win = false;
+            for (uint32_t c : win_t) in_win |= chunk_in[s] == (int64_t)c;
+            if (in_win) continue;
+            const uint64_t nu = next_use((uint32_t)chunk_in[s], t, t + horizon_len);
+            if (best < 0 || nu > best_next) { best = s; best_next = nu; }
+        }
+        SR_CHECK(best >= 0, SERAPH_EINVAL, "schedule error: no slot to evict");
+        return take(best);
+    };
+    auto slot_prefetch = [&](uint64_t t, uint64_t u) -> int64_t {
+        const int64_t e = empty_slot();
+        if (e >= 0) return e;
+        const uint64_t horizon = t + horizon_len;
+        if (!zig) {  // candidates: not used by steps t..u
+            int64_t best = -1;
+            uint64_t best_next = 0;
+            for (uint32_t s = 0; s < nslots; ++s) {
+                const uint64_t nu = next_use((uint32_t)chunk_in[s], t, horizon);
+                if (nu <= u) continue;
+                if (best < 0 || nu > best_next) { best = s; best_next = nu; }
+            }
+            return best < 0 ? -1 : take(best);
+        }
+        int64_t best = -1;
+        uint64_t best_next = 0;
+        for (uint32_t s = 0; s < nslots; ++s) {
+            const uint64_t nu = next_use((uint32_t)chunk_in[s], u, horizon);
+            if (best < 0 || nu > best_next) { best = s; best_next = nu; }
+        }
+        if (best < 0 || best_next <= u) return -1;
+        if (next_use((uint32_t)chunk_in[best], t, u) < u) return -1;  // still needed before u
+        return take(best);
+    };
+
+    // copy chunk c into `slot` on the copy stream, during step t
+    auto load = [&](uint32_t c, int64_t slot, uint64_t t) {
+        if (last_use[slot] >= 0) SR_CUDA(cudaStreamWaitEvent(xs.s, step_done[last_use[slot] % ring].e, 0));
         const Chunk& ch = chunks[c];
         uint8_t* sb = ebuf.p + (uint64_t)slot * slot_bytes;
-        uint8_t* wb = use_w ? sb + ch.w_slot_off : nullptr;
-        const int par = (int)((t / C) & 1), i = (int)(t % C);
-        if (prof) SR_CUDA(cudaEventRecord(pc_b[par * C + i].e, xs.s));
+        if (prof) SR_CUDA(cudaEventRecord(pc_b[(load_seq + 1) % ring].e, xs.s));
         SR_CUDA(cudaMemcpyAsync(sb, g->h_struct.p + ch.s_begin, ch.s_bytes, cudaMemcpyHostToDevice, xs.s));
         if (use_w && ch.w_bytes)
-            SR_CUDA(cudaMemcpyAsync(wb, g->h_weight.p + ch.w_begin, ch.w_bytes, cudaMemcpyHostToDevice, xs.s));
-        if (prof) SR_CUDA(cudaEventRecord(pc_e[par * C + i].e, xs.s));
+            SR_CUDA(cudaMemcpyAsync(sb + ch.w_slot_off, g->h_weight.p + ch.w_begin, ch.w_bytes,
+                                    cudaMemcpyHostToDevice, xs.s));
+        if (prof) SR_CUDA(cudaEventRecord(pc_e[(load_seq + 1) % ring].e, xs.s));
         launch_set_locs(loc.p, g->d_vb.p, ch.first_page, ch.end_page, d_rel_soff.p, d_rel_woff.p,
-                        d_offb.p, sb, use_w ? ebuf.p + (uint64_t)slot * slot_bytes : nullptr, xs.s);
+                        d_offb.p, sb, use_w ? sb : nullptr, rs.p, ++load_seq, xs.s);
         ++launches;
-        SR_CUDA(cudaEventRecord(copy_done[t % R].e, xs.s));
+        SR_CUDA(cudaEventRecord(copy_done[c].e, xs.s));
+        slot_of[c] = slot;
+        chunk_in[slot] = c;
+        pending[c] = 1;
         S.bytes_streamed += ch.s_bytes + (use_w ? ch.w_bytes : 0);
-        loaded[c] = 1;
     };
 
     const unsigned relax_grid = device_sms() * 8;
@@ -255,25 +408,55 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     bool predict = P->pvu != SERAPH_PVU_OFF;
     bool pr_predict_off = false;
     int rc = SERAPH_OK;
-    std::vector<double> copy_ms_by_sweep;
+    std::vector<int64_t> proc_step(C, -1);  // last prediction-off step that processed a chunk
+    int64_t last_change = -1;               // last step with a value change (init = step -1)
+    uint64_t sweep_first_step = 0;
+    std::vector<uint8_t> pred_in_step(ring, 0);
+    std::vector<std::vector<uint32_t>> window_of(ring);
+    uint32_t npass = P->passes;
 
     SR_CUDA(cudaStreamSynchronize(cs.s));
     SR_CUDA(cudaEventRecord(ev_start.e, xs.s));
-    load(0);
+    std::vector<uint32_t> seq_of(C, 0);  // load sequence number of each chunk
     for (uint64_t t = 0;; ++t) {
-        const uint32_t c = (uint32_t)(t % C);
-        const uint64_t sweep = t / C;
-        const int par = (int)(sweep & 1), si = (int)(t % C);
-        if (!resident || t + 1 < C) load(t + 1);
-        if (!resident || t < C) SR_CUDA(cudaStreamWaitEvent(cs.s, copy_done[t % R].e, 0));
-        if (prof) SR_CUDA(cudaEventRecord(pk_b[par * C + si].e, cs.s));
-
+        const std::vector<uint32_t>& win = sched.window(t);
+        // (0) anything step t needs that could not be prefetched
+        for (uint32_t c : win)
+            if (slot_of[c] < 0) {
+                load(c, slot_demand(t), t);
+                seq_of[c] = load_seq;
+            }
+        // (1) prefetch: the next step (cyclic), or as far ahead as the
+        // eviction rule allows (zigzag), so the copy engine keeps streaming
+        const uint64_t reach = zig ? t + horizon_len : t + 2;
+        bool stop_prefetch = false;
+        for (uint64_t u = t + 1; u < reach && !stop_prefetch; ++u)
+            for (uint32_t c : sched.window(u)) {
+                if (slot_of[c] >= 0) continue;
+                const int64_t slot = slot_prefetch(t, u);
+                if (slot < 0) { stop_prefetch = true; break; }
+                load(c, slot, t);
+                seq_of[c] = load_seq;
+            }
+        // idle-slot passes of this step run while the next step's data is in flight
+        bool prefetch = false;
+        uint32_t want = 0;
+        for (uint32_t c : sched.window(t + 1))
+            if (pending[c]) { prefetch = true; want = std::max(want, seq_of[c]); }
+        // (2) passes over the window
+        for (uint32_t c : win) {
+            SR_CHECK(slot_of[c] >= 0, SERAPH_EINVAL, "schedule error: window chunk not resident");
+            if (pending[c]) {
+                SR_CUDA(cudaStreamWaitEvent(cs.s, copy_done[c].e, 0));
+                pending[c] = 0;
+            }
+        }
+        if (prof) SR_CUDA(cudaEventRecord(pk_b[t % ring].e, cs.s));
         WindowDesc wd{};
         {
-            const uint32_t wn = (uint32_t)std::min<uint64_t>(Weff, t + 1);
             uint32_t blocks = 0;
-            for (uint32_t k = 0; k < wn; ++k) {  // oldest first
-                const Chunk& ch = chunks[(c + C - (wn - 1 - k)) % C];
+            for (size_t k = 0; k < win.size(); ++k) {
+                const Chunk& ch = chunks[win[k]];
                 ChunkDesc& d = wd.c[k];
                 d.v_begin = ch.v_begin;
                 d.v_end = ch.v_end;
@@ -282,39 +465,55 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
                 d.block_begin = blocks;
                 blocks += (uint32_t)((uint64_t(ch.v_end - ch.v_begin) + 1023) / 1024);
             }
-            wd.nchunks = wn;
+            wd.nchunks = (uint32_t)win.size();
             wd.nblocks = blocks;
         }
         const bool pred_now = is_pr ? (predict && !pr_predict_off) : predict;
-        for (uint32_t j = 0; j < P->passes; ++j) {
-            launch_compact(algo, wd, a, pass, j > 0, pred_now ? 1 : 0, cs.s);
-            if (prof) SR_CUDA(cudaEventRecord(pr_b[si * P->passes + j].e, cs.s));
-            launch_relax(algo, P->kahan, a, pass, j > 0, relax_grid, cs.s);
-            if (prof) SR_CUDA(cudaEventRecord(pr_e[si * P->passes + j].e, cs.s));
-            launches += 2;
+        npass = max_passes > P->passes && (prefetch || resident) ? max_passes : P->passes;
+        for (uint32_t j = 0; j < npass; ++j) {
+            const bool idle = j >= P->passes;
+            launch_gate(rs.p, pass, j > 0, idle && prefetch, want, cs.s);
+            launch_compact(algo, wd, a, pass, pred_now ? 1 : 0, cs.s);
+            if (prof) SR_CUDA(cudaEventRecord(pr_b[(t % ring) * max_passes + j].e, cs.s));
+            launch_relax(algo, P->kahan, a, pass, (uint32_t)t, relax_grid, cs.s);
+            if (prof) SR_CUDA(cudaEventRecord(pr_e[(t % ring) * max_passes + j].e, cs.s));
+            launches += 3;
             S.relax_launches += 1;
             if (is_pr) {
-                launch_pr_apply(a, pass, j > 0, relax_grid, cs.s);
+                launch_pr_apply(a, pass, relax_grid, cs.s);
                 ++launches;
             }
             ++pass;
         }
-        if (prof) SR_CUDA(cudaEventRecord(pk_e[par * C + si].e, cs.s));
-        SR_CUDA(cudaEventRecord(step_done[t % R].e, cs.s));
+        if (prof) SR_CUDA(cudaEventRecord(pk_e[t % ring].e, cs.s));
+        SR_CUDA(cudaEventRecord(step_done[t % ring].e, cs.s));
+        for (uint32_t c : win) last_use[slot_of[c]] = (int64_t)t;
+        pred_in_step[t % ring] = pred_now;
+        window_of[t % ring] = win;
+        npass_of[t % ring] = npass;
         S.steps += 1;
+        if (!sched.sweep_end(t)) continue;
 
-        if (c != C - 1) continue;
         // ---------------------------------------------------- sweep close
         if (is_pr)
-            launch_close_pr(a, n, x_prev.p, g->d_zero_in.p, P->damping, partial.p, nparts, d_rep.p, cs.s);
+            launch_close_pr(a, n, x_prev.p, P->damping, partial.p, nparts, d_rep.p, cs.s);
         else
             launch_close_min(rs.p, d_rep.p, cs.s);
-        launches += is_pr ? 4 : 1;
+        launches += is_pr ? 2 : 1;
         SR_CUDA(cudaMemcpyAsync(h_rep.p, d_rep.p, sizeof(SweepReport), cudaMemcpyDeviceToHost, cs.s));
+        SR_CUDA(cudaMemcpyAsync(h_steps.p, d_steps.p, ring * sizeof(unsigned), cudaMemcpyDeviceToHost, cs.s));
         SR_CUDA(cudaEventRecord(ev_sweep.e, cs.s));
         wait_event(ev_sweep.e, P->timeout_ms);
         SweepReport rep;
         std::memcpy(&rep, h_rep.p, sizeof(rep));
+        const unsigned* steps_changed = (const unsigned*)h_steps.p;
+        for (uint64_t s = sweep_first_step; s <= t; ++s) {
+            if (steps_changed[s % ring]) last_change = (int64_t)s;
+            if (!pred_in_step[s % ring] || !P->verify)
+                for (uint32_t c : window_of[s % ring]) proc_step[c] = (int64_t)s;
+        }
+        // clear the ring entries of this sweep for reuse
+        SR_CUDA(cudaMemsetAsync(d_steps.p, 0, ring * sizeof(unsigned), cs.s));
         S.sweeps += 1;
         S.passes_run += rep.passes_run;
         S.passes_skipped += rep.passes_skipped;
@@ -324,14 +523,24 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         S.changes += rep.changed;
         if (!pred_now) S.verify_sweeps += 1;
         if (prof) {
-            for (uint32_t i = 0; i < C; ++i) {
-                S.compute_ms += elapsed(pk_b[par * C + i].e, pk_e[par * C + i].e);
-                for (uint32_t j = 0; j < P->passes; ++j)
-                    S.relax_ms += elapsed(pr_b[i * P->passes + j].e, pr_e[i * P->passes + j].e);
-                if (!resident || sweep == 0)
-                    S.copy_ms += elapsed(pc_b[par * C + i].e, pc_e[par * C + i].e);
+            for (uint64_t s = sweep_first_step; s <= t; ++s) {
+                S.compute_ms += elapsed(pk_b[s % ring].e, pk_e[s % ring].e);
+                for (uint32_t j = 0; j < npass_of[s % ring]; ++j) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, pr_b[(s % ring) * max_passes + j].e,
+                                             pr_e[(s % ring) * max_passes + j].e) == cudaSuccess)
+                        S.relax_ms += ms;
+                    else
+                        (void)cudaGetLastError();
+                }
+            }
+            // every finished load (the prefetch for the next sweep may still run)
+            while (loads_timed < load_seq && cudaEventQuery(pc_e[(loads_timed + 1) % ring].e) == cudaSuccess) {
+                ++loads_timed;
+                S.copy_ms += elapsed(pc_b[loads_timed % ring].e, pc_e[loads_timed % ring].e);
             }
         }
+        sweep_first_step = t + 1;
         bool stop = false;
         if (is_pr) {
             S.residual = rep.resid;
@@ -339,12 +548,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             else if (pred_now && rep.resid < std::max(P->pr_pvu_off_below, P->tol)) pr_predict_off = true;
             if (!stop && S.sweeps >= P->max_sweeps) stop = true;
         } else {
-            if (rep.changed == 0 && (!pred_now || !P->verify)) {
+            bool all_after = true;
+            for (uint32_t c = 0; c < C; ++c) all_after &= proc_step[c] > last_change;
+            if (all_after) {
                 S.converged = 1;
                 stop = true;
                 if (rep.overflow) rc = SERAPH_EOVERFLOW;
             } else if (rep.changed == 0) {
-                predict = false;  // verification sweep with prediction off
+                predict = false;  // a predicted sweep changed nothing: retrieve with all-pull
             } else {
                 predict = P->pvu != SERAPH_PVU_OFF;
             }

@@ -75,6 +75,22 @@ def test_partitioner_matches_oracle(name, make, P, sym):
     assert g.info()["max_in_degree"] == int(np.diff(ocol_off).max(initial=0))
 
 
+@pytest.mark.parametrize("wmax,width", [(255, 1), (1000, 2), (70000, 4)])
+def test_weight_width_and_sssp(wmax, width):
+    """Weights are stored in the narrowest lossless width; SSSP reads each."""
+    src, dst, w = graphs.random_graph(3000, 40000, seed=wmax, wmax=wmax)
+    g = seraph.Graph.from_edges(3000, src, dst, w, num_pages=9)
+    assert g.info()["weight_width"] == width
+    og = oracle_graph(3000, src, dst, w)
+    _, _, wc, _ = g.export_csc()
+    assert np.array_equal(wc, oracle.csc(og)[2])
+    for window, mx in ((2, 0), (3, 5)):
+        got, st = seraph.run(g, "sssp", source=1, window=window, max_passes=mx,
+                             budget_bytes=budget(g, window, 1.3))
+        assert st["resident"] == 0
+        assert np.array_equal(got, oracle.sssp(og, 1))
+
+
 def test_partitioner_device_input_and_csr_input():
     import torch
     n, src, dst, w = rmat(12)
@@ -157,6 +173,12 @@ def test_pagerank_is_deterministic(r16):
 SCHEDULES = [
     dict(window=1, passes=3),                       # double-buffer variant
     dict(window=2, passes=1),
+    dict(window=3, passes=1, order="zigzag"),
+    dict(window=2, passes=1, order="zigzag", max_passes=6),
+    dict(window=4, passes=1, order="cyclic", max_passes=4, pvu="weak"),
+    dict(window=3, passes=2, order="zigzag", pvu="strong"),
+    dict(window=1, passes=1, order="zigzag", slots=7),
+    dict(window=2, passes=1, order="cyclic", slots=9, max_passes=3),
     dict(window=4, passes=2),
     dict(window=3, passes=1, pvu="strong"),
     dict(window=3, passes=1, pvu="weak"),
@@ -183,19 +205,20 @@ def r13_paged():
 def test_schedule_invariance_streamed(r13_paged, algo, sched):
     g = r13_paged["gs"] if algo == "cc" else r13_paged["g"]
     kw = dict(sched)
-    kw["budget_bytes"] = budget(g, kw["window"], 1.7, algo == "sssp")
+    nslot = kw.get("slots", kw["window"] + 1)
+    kw["budget_bytes"] = budget(g, nslot - 1, 1.7, algo == "sssp")
     got, st = seraph.run(g, algo, source=5, **kw)
-    assert st["resident"] == 0 and st["chunks"] > kw["window"] + 1
+    assert st["resident"] == 0 and st["chunks"] > nslot
     assert np.array_equal(got, r13_paged[algo])
     if kw.get("pvu") in ("strong", "weak"):
         assert st["verify_sweeps"] >= 1
 
 
-@pytest.mark.parametrize("sched", SCHEDULES[:6], ids=lambda s: "-".join(f"{k}{v}" for k, v in s.items()))
+@pytest.mark.parametrize("sched", SCHEDULES[:8], ids=lambda s: "-".join(f"{k}{v}" for k, v in s.items()))
 def test_pagerank_streamed(r13_paged, sched):
     g = r13_paged["g"]
     kw = dict(sched)
-    kw["budget_bytes"] = budget(g, kw["window"], 1.7, False)
+    kw["budget_bytes"] = budget(g, kw.get("slots", kw["window"] + 1) - 1, 1.7, False)
     if kw.get("pvu") == "strong":
         with pytest.raises(SeraphError):
             seraph.run(g, "pagerank", **kw)
