@@ -170,7 +170,8 @@ typedef struct seraph_params {
                                    when |dx| <= pr_fail_eps * x               */
     double   pr_pvu_off_below;  /* PageRank: prediction off once L1 change < this */
     uint32_t thread_max_deg;    /* in-degree <= this: one thread per vertex   */
-    uint32_t warp_max_deg;      /* <= this: one warp; above: one CTA per vertex */
+    uint32_t warp_max_deg;      /* <= this: one warp (or a smaller lane group,
+                                   see group*_max_deg); above: one CTA       */
     int32_t  sched;             /* seraph_sched                               */
     uint32_t timeout_ms;        /* bound on every host wait                   */
     uint32_t profile;           /* 1: time every relax kernel and step with
@@ -185,6 +186,10 @@ typedef struct seraph_params {
                                    window + 1 (0 = window + 1).  Slots beyond
                                    the window keep chunks resident across
                                    sweeps so they are not streamed again      */
+    uint32_t group4_max_deg;    /* in-degree <= this (and > thread_max_deg):
+                                   4 lanes per vertex                         */
+    uint32_t group8_max_deg;    /* <= this: 8 lanes per vertex; require
+                                   thread <= group4 <= group8 <= warp          */
     void*    sched_model;       /* seraph_sched_model* for SERAPH_SCHED_LEARNED */
     void*    stream;            /* cudaStream_t for compute, NULL = own       */
     void*    trace;             /* seraph_trace* to fill, or NULL             */

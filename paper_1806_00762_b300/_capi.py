@@ -57,7 +57,8 @@ class Params(ctypes.Structure):
                 ("damping", dbl), ("tol", dbl), ("pr_fail_eps", dbl),
                 ("pr_pvu_off_below", dbl), ("thread_max_deg", u32), ("warp_max_deg", u32),
                 ("sched", i32), ("timeout_ms", u32), ("profile", u32), ("order", u32),
-                ("max_passes", u32), ("slots", u32),
+                ("max_passes", u32), ("slots", u32), ("group4_max_deg", u32),
+                ("group8_max_deg", u32),
                 ("sched_model", vp), ("stream", vp), ("trace", vp)]
 
 

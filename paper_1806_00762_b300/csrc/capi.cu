@@ -161,6 +161,8 @@ int seraph_params_default(seraph_params* p, int algo) {
         p->pr_fail_eps = 1.0 / (1 << 20);
         p->pr_pvu_off_below = 1e-6;
         p->thread_max_deg = 8;
+        p->group4_max_deg = 32;
+        p->group8_max_deg = 128;
         p->warp_max_deg = 4096;
         p->sched = SERAPH_SCHED_FIXED;
         p->timeout_ms = 600000;

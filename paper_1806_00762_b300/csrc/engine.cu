@@ -237,28 +237,40 @@ __device__ __forceinline__ void edges_strided(const AlgoArgs& a, const PageLoc& 
         gather8<ALGO, KAHAN, WB>(a, loc, b, e, idx, idx + 4 * G, macc, sacc);
 }
 
-template <int ALGO, bool KAHAN, int WB>
-__device__ __forceinline__ void vertex_warp(const AlgoArgs& a, unsigned long long ent, float base,
-                                            Locals& L) {
-    const uint32_t v = (uint32_t)ent, p = (uint32_t)(ent >> 32);
-    const PageLoc loc = a.loc[p];
-    const uint32_t li = v - loc.vb;
-    const uint32_t b = loc.off[li], e = loc.off[li + 1];
-    const uint32_t lane = lane_id();
+// One vertex per group of G lanes (G = 4, 8 or 32), 32/G vertices per warp
+// at once so that their dependent load chains (list entry, page location,
+// offsets, columns, gathered values) overlap.  Every lane of the warp calls
+// this (inactive groups pass valid = false) because the group reduction
+// shuffles across the whole warp; xor offsets below G stay inside a group.
+template <int ALGO, bool KAHAN, int WB, int G>
+__device__ __forceinline__ void vertex_group(const AlgoArgs& a, unsigned long long ent, bool valid,
+                                             float base, Locals& L) {
+    const uint32_t t = lane_id() & (G - 1);
     MinAcc macc{SERAPH_INF, false};
     SumAcc sacc{0.f, 0.f};
-    edges_strided<ALGO, KAHAN, WB>(a, loc, b, e, lane, 32, macc, sacc);
+    uint32_t v = 0, b = 0, e = 0;
+    if (valid) {
+        v = (uint32_t)ent;
+        const PageLoc loc = a.loc[(uint32_t)(ent >> 32)];
+        const uint32_t li = v - loc.vb;
+        b = loc.off[li];
+        e = loc.off[li + 1];
+        edges_strided<ALGO, KAHAN, WB>(a, loc, b, e, t, G, macc, sacc);
+    }
     if (ALGO == ALG_PR) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = G / 2; o > 0; o >>= 1) {
             SumAcc other{__shfl_xor_sync(kFull, sacc.s, o), __shfl_xor_sync(kFull, sacc.c, o)};
-            sacc = (lane & o) ? sum_merge<KAHAN>(other, sacc) : sum_merge<KAHAN>(sacc, other);
+            sacc = (t & o) ? sum_merge<KAHAN>(other, sacc) : sum_merge<KAHAN>(sacc, other);
         }
-        if (lane == 0) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L);
+        if (valid && t == 0) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L);
     } else {
-        macc.best = __reduce_min_sync(kFull, macc.best);
-        macc.ovf = __any_sync(kFull, macc.ovf);
-        if (lane == 0) finish_min<ALGO>(a, v, macc, e - b, L);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            macc.best = min(macc.best, __shfl_xor_sync(kFull, macc.best, o));
+            macc.ovf |= __shfl_xor_sync(kFull, (int)macc.ovf, o) != 0;
+        }
+        if (valid && t == 0) finish_min<ALGO>(a, v, macc, e - b, L);
     }
 }
 
@@ -330,7 +342,7 @@ __global__ void gate_kernel(RunState* rs, uint32_t pass, int check_prev, int idl
     if (check_prev && rs->pass_changed[par ^ 1] == 0) go = false;
     if (idle && (int)(*(volatile unsigned*)&rs->loaded - want_loaded) >= 0) go = false;
     rs->pass_go[par] = go;
-    for (int k = 0; k < 4; ++k) rs->work[par][k] = 0;
+    for (int k = 0; k < 8; ++k) rs->work[par][k] = 0;
     rs->pass_changed[par] = 0;
     if (go) rs->cur.passes_run += 1;
     else rs->cur.passes_skipped += 1;
@@ -340,7 +352,7 @@ template <int ALGO>
 __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a, uint32_t pass,
                                                       int predict) {
     __shared__ unsigned ws[kNT / 32 + 1];
-    __shared__ unsigned s_base[3];
+    __shared__ unsigned s_base[kClasses];
     const int par = pass & 1;
     RunState* rs = a.rs;
     if (!rs->pass_go[par]) return;
@@ -382,14 +394,17 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
                     ++n_skip;
                 } else {
                     ++n_att;
-                    my_cls[r] = deg <= a.thread_max ? 0 : (deg <= a.warp_max ? 1 : 2);
+                    my_cls[r] = deg <= a.cls_max[0] ? 0
+                              : deg <= a.cls_max[1] ? 1
+                              : deg <= a.cls_max[2] ? 2
+                              : deg <= a.cls_max[3] ? 3 : 4;
                     my_ent[r] = ((unsigned long long)p << 32) | v;
                 }
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kClasses; ++k) {
         unsigned mine = 0;
 #pragma unroll
         for (int r = 0; r < kCompactRounds; ++r) mine += my_cls[r] == k;
@@ -411,36 +426,55 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
     }
 }
 
+// Class-k list (k = 1, 2, 3) with G lanes per vertex: each warp grabs
+// 4 * 32/G entries at a time.
+template <int ALGO, bool KAHAN, int WB, int G>
+__device__ __forceinline__ void group_phase(const AlgoArgs& a, int par, int k, float base,
+                                            Locals& L) {
+    constexpr unsigned per = 32 / G;
+    const unsigned n = a.rs->list_cnt[par][k];
+    const unsigned lane = lane_id(), grp = lane / G;
+    for (;;) {
+        unsigned i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&a.rs->work[par][k], 4 * per);
+        i0 = __shfl_sync(kFull, i0, 0);
+        if (i0 >= n) break;
+#pragma unroll 1
+        for (unsigned r = 0; r < 4; ++r) {
+            const unsigned i = i0 + r * per + grp;
+            const bool valid = i < n;
+            vertex_group<ALGO, KAHAN, WB, G>(a, valid ? a.list[k][i] : 0ull, valid, base, L);
+        }
+    }
+}
+
 template <int ALGO, bool KAHAN, int WB>
-__global__ void __launch_bounds__(kNT) relax_kernel(AlgoArgs a, uint32_t pass, uint32_t step) {
+__global__ void __launch_bounds__(kNT)
+    relax_kernel(AlgoArgs a, uint32_t pass, uint32_t step) {
     __shared__ unsigned s_item;
     __shared__ float s_sum[kNT / 32], s_comp[kNT / 32];
     __shared__ unsigned s_min[kNT / 32], s_ovf[kNT / 32];
     const int par = pass & 1;
     RunState* rs = a.rs;
-    if (blockIdx.x == 0 && threadIdx.x < 4) rs->list_cnt[par ^ 1][threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 8) rs->list_cnt[par ^ 1][threadIdx.x] = 0;
     if (!rs->pass_go[par]) return;
-    const unsigned n0 = rs->list_cnt[par][0], n1 = rs->list_cnt[par][1], n2 = rs->list_cnt[par][2];
     const float base = ALGO == ALG_PR ? rs->base : 0.f;
     Locals L{0u, SERAPH_INF, 0u, 0ull};
 
+    const unsigned n_cta = rs->list_cnt[par][4];
     for (;;) {  // one CTA per hub vertex
-        if (threadIdx.x == 0) s_item = atomicAdd(&rs->work[par][2], 1u);
+        if (threadIdx.x == 0) s_item = atomicAdd(&rs->work[par][4], 1u);
         __syncthreads();
         const unsigned i = s_item;
         __syncthreads();
-        if (i >= n2) break;
-        vertex_cta<ALGO, KAHAN, WB>(a, a.list[2][i], base, L, s_sum, s_comp, s_min, s_ovf);
+        if (i >= n_cta) break;
+        vertex_cta<ALGO, KAHAN, WB>(a, a.list[4][i], base, L, s_sum, s_comp, s_min, s_ovf);
     }
+    group_phase<ALGO, KAHAN, WB, 32>(a, par, 3, base, L);
+    group_phase<ALGO, KAHAN, WB, 8>(a, par, 2, base, L);
+    group_phase<ALGO, KAHAN, WB, 4>(a, par, 1, base, L);
     const unsigned lane = lane_id();
-    for (;;) {  // one warp per medium vertex, four at a time
-        unsigned i0 = 0;
-        if (lane == 0) i0 = atomicAdd(&rs->work[par][1], 4u);
-        i0 = __shfl_sync(kFull, i0, 0);
-        if (i0 >= n1) break;
-        for (unsigned j = 0; j < 4 && i0 + j < n1; ++j)
-            vertex_warp<ALGO, KAHAN, WB>(a, a.list[1][i0 + j], base, L);
-    }
+    const unsigned n0 = rs->list_cnt[par][0];
     for (;;) {  // one thread per small vertex, 128 per warp grab
         unsigned i0 = 0;
         if (lane == 0) i0 = atomicAdd(&rs->work[par][0], 128u);
@@ -459,10 +493,10 @@ __global__ void __launch_bounds__(kNT) pr_apply_kernel(AlgoArgs a, uint32_t pass
     const int par = pass & 1;
     RunState* rs = a.rs;
     if (!rs->pass_go[par]) return;
-    const unsigned n[3] = {rs->list_cnt[par][0], rs->list_cnt[par][1], rs->list_cnt[par][2]};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (int k = 0; k < 3; ++k) {
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n[k]; i += stride) {
+    for (int k = 0; k < kClasses; ++k) {
+        const unsigned nk = rs->list_cnt[par][k];
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nk; i += stride) {
             const uint32_t v = (uint32_t)a.list[k][i];
             const float xn = a.x_next[v];
             a.x[v] = xn;

@@ -8,6 +8,9 @@
 namespace seraph {
 
 constexpr int kMaxWindow = 16;
+// In-degree classes of the relax mapping: one thread, 4 lanes, 8 lanes, a
+// warp, or a whole CTA per vertex.
+constexpr int kClasses = 5;
 
 // Where a resident page's arrays currently live (device addresses in the
 // edge ring).  Rewritten whenever the page's chunk is (re)loaded.
@@ -45,8 +48,8 @@ struct RunState {
     unsigned int loaded;          // sequence number of the last chunk load done
     unsigned int pad1;
     unsigned int pass_changed[2];
-    unsigned int list_cnt[2][4];
-    unsigned int work[2][4];
+    unsigned int list_cnt[2][8];
+    unsigned int work[2][8];
     unsigned int thr_cur, thr_prev, sweeps_done, err;
     float base, pad;
     double dsum, rsum;
@@ -64,10 +67,10 @@ struct AlgoArgs {
     RunState* rs;
     const PageLoc* loc;       // per page
     const uint32_t* vb;       // page boundaries (P+1)
-    unsigned long long* list[3];  // entries (page << 32) | v, per mapping class
+    unsigned long long* list[kClasses];  // entries (page << 32) | v, per class
     unsigned int* step_changed;   // value changes per pipeline step (ring)
     uint32_t step_mask;           // ring size - 1
-    uint32_t thread_max, warp_max;
+    uint32_t cls_max[4];      // largest in-degree of classes 0..3 (above: class 4)
     float damping, fail_eps;
     uint8_t fsm_next[12];
     uint8_t skip_mask;

@@ -140,7 +140,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CHECK(P->max_sweeps >= 1, SERAPH_EINVAL, "max_sweeps must be >= 1");
     for (int i = 0; i < 12; ++i)
         SR_CHECK(P->fsm_next[i] < 6, SERAPH_EINVAL, "fsm_next entries must be < 6");
-    SR_CHECK(P->thread_max_deg <= P->warp_max_deg, SERAPH_EINVAL, "thread_max_deg > warp_max_deg");
+    SR_CHECK(P->thread_max_deg <= P->group4_max_deg && P->group4_max_deg <= P->group8_max_deg &&
+                 P->group8_max_deg <= P->warp_max_deg,
+             SERAPH_EINVAL, "need thread_max_deg <= group4_max_deg <= group8_max_deg <= warp_max_deg");
     const uint64_t n = g->n;
     int algo = P->algo;
     if ((algo == SERAPH_SSSP || algo == SERAPH_BFS))
@@ -216,7 +218,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CUDA(cudaMemcpyAsync(d_rel_soff.p, rel_soff.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
     SR_CUDA(cudaMemcpyAsync(d_rel_woff.p, rel_woff.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
     SR_CUDA(cudaMemcpyAsync(d_offb.p, offb.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
-    DevBuf<unsigned long long> lists(3 * max_win_v);
+    DevBuf<unsigned long long> lists((uint64_t)kClasses * max_win_v);
     DevBuf<RunState> rs(1);
     DevBuf<SweepReport> d_rep(1);
     DevBuf<unsigned> d_steps(ring);
@@ -247,11 +249,13 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     a.rs = rs.p;
     a.loc = loc.p;
     a.vb = g->d_vb.p;
-    for (int k = 0; k < 3; ++k) a.list[k] = lists.p + k * max_win_v;
+    for (int k = 0; k < kClasses; ++k) a.list[k] = lists.p + k * max_win_v;
     a.step_changed = d_steps.p;
     a.step_mask = ring - 1;
-    a.thread_max = P->thread_max_deg;
-    a.warp_max = P->warp_max_deg;
+    a.cls_max[0] = P->thread_max_deg;
+    a.cls_max[1] = P->group4_max_deg;
+    a.cls_max[2] = P->group8_max_deg;
+    a.cls_max[3] = P->warp_max_deg;
     a.damping = (float)P->damping;
     a.fail_eps = (float)P->pr_fail_eps;
     std::memcpy(a.fsm_next, P->fsm_next, 12);

@@ -183,9 +183,16 @@ SCHEDULES = [
     dict(window=3, passes=1, pvu="strong"),
     dict(window=3, passes=1, pvu="weak"),
     dict(window=2, passes=4, pvu="weak"),
-    dict(window=1, passes=1, thread_max_deg=0, warp_max_deg=0),       # every vertex on a CTA
-    dict(window=2, passes=1, thread_max_deg=4096, warp_max_deg=4096),  # every vertex on a thread
-    dict(window=2, passes=1, thread_max_deg=0, warp_max_deg=1 << 30),  # every vertex on a warp
+    dict(window=1, passes=1, thread_max_deg=0, group4_max_deg=0, group8_max_deg=0,
+         warp_max_deg=0),                                              # every vertex on a CTA
+    dict(window=2, passes=1, thread_max_deg=4096, group4_max_deg=4096, group8_max_deg=4096,
+         warp_max_deg=4096),                                           # every vertex on a thread
+    dict(window=2, passes=1, thread_max_deg=0, group4_max_deg=0, group8_max_deg=0,
+         warp_max_deg=1 << 30),                                        # every vertex on a warp
+    dict(window=2, passes=1, thread_max_deg=0, group4_max_deg=1 << 30, group8_max_deg=1 << 30,
+         warp_max_deg=1 << 30),                                        # every vertex on 4 lanes
+    dict(window=2, passes=1, thread_max_deg=0, group4_max_deg=0, group8_max_deg=1 << 30,
+         warp_max_deg=1 << 30),                                        # every vertex on 8 lanes
 ]
 
 
