@@ -263,6 +263,62 @@ int seraph_pull_fixpoint_noalloc(int algo, uint64_t n, const uint64_t* col_off,
                                  const uint32_t* row, const uint32_t* w, uint32_t source,
                                  uint32_t* values, uint32_t* passes_out, void* stream);
 
+/*
+ * Learned scheduler (not in the paper; its closest counterpart is the
+ * fine-grained idle-slot scheduling of Sec. 3.2).  A 16 -> 64 -> 64 -> 17 MLP
+ * with GELU, BF16 weights and FP32 accumulation (FP32 master weights, Adam),
+ * trained and run by the library's own kernels.  Inputs: 16 per-chunk
+ * features of a pipeline step (SERAPH_SCHED_FEATURE_* below).  Outputs: the
+ * number of local passes k in [1,16] for the step (argmax of 16 logits) and a
+ * streaming priority (predicted first-pass gain).  With params.sched =
+ * SERAPH_SCHED_LEARNED (window must be 1) the device caps each step's passes
+ * at the predicted k (no host round trip) and every sweep streams chunks in
+ * descending predicted priority; for SSSP/BFS/CC chunks predicted to change
+ * nothing may be skipped in a sweep, which the stop rule (every chunk
+ * processed after the last change) makes safe.  The fixed schedule remains
+ * the fallback and the judge.
+ */
+#define SERAPH_SCHED_FEATURES 16
+#define SERAPH_SCHED_OUTPUTS 17
+#define SERAPH_SCHED_PARAMS 6353   /* 64*16+64 + 64*64+64 + 17*64+17 */
+
+typedef struct seraph_sched_model seraph_sched_model;  /* opaque */
+
+/* A trace of pipeline steps filled by seraph_run (params.trace; window must
+ * be 1): per step the 16 features seen at the step's start and the number of
+ * value changes in each of its passes (up to 16; 0 for passes not run). */
+typedef struct seraph_trace {
+    uint64_t capacity;          /* rows the caller allocated                 */
+    uint64_t count;             /* rows written (output)                     */
+    float*    features;         /* host, capacity x 16                       */
+    uint32_t* gains;            /* host, capacity x 16                       */
+    uint32_t* vertices;         /* host, capacity: vertices of the chunk     */
+} seraph_trace;
+
+/* New model with Glorot-uniform weights from a seeded splitmix64 stream.
+ * fp32 != 0: debug mode, the forward pass uses the FP32 master weights. */
+int  seraph_sched_create(uint64_t seed, int fp32, seraph_sched_model** out);
+int  seraph_sched_get_params(const seraph_sched_model* m, float* params /* host, PARAMS */);
+int  seraph_sched_set_params(seraph_sched_model* m, const float* params /* host, PARAMS */);
+/* Mean loss over n samples and its gradient w.r.t. the master weights:
+ * CE(softmax(logits), k-1) + (priority_out - prio)^2.  x: n x 16, k: n
+ * (1..16), prio: n, all in `mem`; loss and grad (PARAMS floats) on the host. */
+int  seraph_sched_loss_grad(seraph_sched_model* m, const float* x, const int32_t* k,
+                            const float* prio, uint64_t n, int mem, float* loss, float* grad);
+/* `epochs` passes of Adam over shuffled mini-batches; losses[e] (host, may be
+ * NULL) receives the mean batch loss of epoch e. */
+int  seraph_sched_train(seraph_sched_model* m, const float* x, const int32_t* k, const float* prio,
+                        uint64_t n, int mem, uint32_t epochs, uint32_t batch, float lr,
+                        uint64_t seed, float* losses);
+/* Predictions for n feature rows (x in `mem`; outputs in the same memory). */
+int  seraph_sched_infer(const seraph_sched_model* m, const float* x, uint64_t n, int mem,
+                        int32_t* k_out, float* prio_out);
+/* Training targets from a trace: k = smallest number of passes that captures
+ * at least `share` of the step's changes (1..16); priority = log2(1 + first
+ * pass changes) / 24.  Host arrays of trace->count entries. */
+int  seraph_sched_targets(const seraph_trace* t, float share, int32_t* k_out, float* prio_out);
+void seraph_sched_free(seraph_sched_model* m);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* seraph_last_error(void);
 

@@ -18,7 +18,8 @@ import numpy as np
 from . import _capi as C
 from ._capi import SeraphError, INF
 
-__all__ = ["Graph", "run", "default_params", "SeraphError", "INF", "version"]
+__all__ = ["Graph", "run", "default_params", "SeraphError", "INF", "version", "SchedModel",
+           "TraceBuffer"]
 
 
 def version() -> str:
@@ -121,6 +122,96 @@ class Graph:
             pass
 
 
+class TraceBuffer:
+    """Host buffers for a trace of pipeline steps (features + per-pass gains)."""
+
+    def __init__(self, capacity: int):
+        self.features = np.zeros((capacity, C.SCHED_FEATURES), dtype=np.float32)
+        self.gains = np.zeros((capacity, 16), dtype=np.uint32)
+        self.vertices = np.zeros(capacity, dtype=np.uint32)
+        self.struct = C.Trace(capacity, 0, self.features.ctypes.data, self.gains.ctypes.data,
+                              self.vertices.ctypes.data)
+
+    @property
+    def count(self) -> int:
+        return int(self.struct.count)
+
+    def rows(self):
+        n = self.count
+        return self.features[:n], self.gains[:n], self.vertices[:n]
+
+    def targets(self, share: float = 0.95):
+        n = self.count
+        k = np.empty(n, dtype=np.int32)
+        prio = np.empty(n, dtype=np.float32)
+        C.check(C.lib().seraph_sched_targets(ctypes.byref(self.struct), share, k.ctypes.data,
+                                             prio.ctypes.data))
+        return k, prio
+
+
+class SchedModel:
+    """The learned scheduler's network (see include/seraph.h)."""
+
+    def __init__(self, seed: int = 0, fp32: bool = False):
+        h = ctypes.c_void_p()
+        C.check(C.lib().seraph_sched_create(seed, 1 if fp32 else 0, ctypes.byref(h)))
+        self._h = h
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(C.SCHED_PARAMS, dtype=np.float32)
+        C.check(C.lib().seraph_sched_get_params(self._h, out.ctypes.data))
+        return out
+
+    def set_params(self, params) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        C.check(C.lib().seraph_sched_set_params(self._h, p.ctypes.data))
+
+    def loss_grad(self, x, k, prio):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        prio = np.ascontiguousarray(prio, dtype=np.float32)
+        loss = ctypes.c_float()
+        grad = np.empty(C.SCHED_PARAMS, dtype=np.float32)
+        C.check(C.lib().seraph_sched_loss_grad(self._h, x.ctypes.data, k.ctypes.data,
+                                               prio.ctypes.data, len(k), C.MEM_HOST,
+                                               ctypes.byref(loss), grad.ctypes.data))
+        return loss.value, grad
+
+    def train(self, x, k, prio, epochs=10, batch=256, lr=1e-3, seed=0):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        prio = np.ascontiguousarray(prio, dtype=np.float32)
+        losses = np.empty(epochs, dtype=np.float32)
+        C.check(C.lib().seraph_sched_train(self._h, x.ctypes.data, k.ctypes.data, prio.ctypes.data,
+                                           len(k), C.MEM_HOST, epochs, batch, lr, seed,
+                                           losses.ctypes.data))
+        return losses
+
+    def infer(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        n = x.shape[0]
+        k = np.empty(n, dtype=np.int32)
+        prio = np.empty(n, dtype=np.float32)
+        C.check(C.lib().seraph_sched_infer(self._h, x.ctypes.data, n, C.MEM_HOST, k.ctypes.data,
+                                           prio.ctypes.data))
+        return k, prio
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def free(self):
+        if self._h and self._h.value:
+            C.lib().seraph_sched_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 def default_params(algo) -> C.Params:
     p = C.Params()
     C.check(C.lib().seraph_params_default(ctypes.byref(p), C.ALGOS[algo] if isinstance(algo, str) else algo))
@@ -135,6 +226,13 @@ def run(graph: Graph, algo, out=None, stream=None, **kw):
     array or torch tensor (host or CUDA) of n uint32/float32 values; by
     default a numpy array is returned.  Returns (values, stats dict)."""
     p = default_params(algo)
+    trace = kw.pop("trace", None)
+    model = kw.pop("sched_model", None)
+    if model is not None:
+        p.sched_model = model.handle
+        p.sched = C.SCHED_LEARNED
+    if trace is not None:
+        p.trace = ctypes.cast(ctypes.pointer(trace.struct), ctypes.c_void_p)
     for k, v in kw.items():
         if k == "pvu" and isinstance(v, str):
             v = C.PVUS[v]

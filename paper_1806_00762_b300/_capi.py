@@ -74,6 +74,13 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Trace(ctypes.Structure):
+    _fields_ = [("capacity", u64), ("count", u64), ("features", vp), ("gains", vp),
+                ("vertices", vp)]
+
+
+SCHED_FEATURES, SCHED_OUTPUTS, SCHED_PARAMS = 16, 17, 6353
+
 # name -> (restype, argtypes); every symbol include/seraph.h declares
 PROTOTYPES = {
     "seraph_graph_from_edges": (ctypes.c_int, [u64, u64, vp, vp, vp, ctypes.c_int, u32, u32, vp,
@@ -89,6 +96,15 @@ PROTOTYPES = {
                                   ctypes.POINTER(Stats)]),
     "seraph_pull_fixpoint_noalloc": (ctypes.c_int, [ctypes.c_int, u64, vp, vp, vp, u32, vp, vp,
                                                     vp]),
+    "seraph_sched_create": (ctypes.c_int, [u64, ctypes.c_int, ctypes.POINTER(vp)]),
+    "seraph_sched_get_params": (ctypes.c_int, [vp, vp]),
+    "seraph_sched_set_params": (ctypes.c_int, [vp, vp]),
+    "seraph_sched_loss_grad": (ctypes.c_int, [vp, vp, vp, vp, u64, ctypes.c_int, vp, vp]),
+    "seraph_sched_train": (ctypes.c_int, [vp, vp, vp, vp, u64, ctypes.c_int, u32, u32,
+                                          ctypes.c_float, u64, vp]),
+    "seraph_sched_infer": (ctypes.c_int, [vp, vp, u64, ctypes.c_int, vp, vp]),
+    "seraph_sched_targets": (ctypes.c_int, [ctypes.POINTER(Trace), ctypes.c_float, vp, vp]),
+    "seraph_sched_free": (None, [vp]),
     "seraph_last_error": (ctypes.c_char_p, []),
     "seraph_version": (ctypes.c_char_p, []),
 }

@@ -1,10 +1,15 @@
 // extern "C" entry points of include/seraph.h.  Every call catches
 // exceptions, records a thread-local message and returns a SERAPH_E* code.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <vector>
 #include <new>
 #include <string>
 
 #include "graph.hpp"
+#include "mlp.cuh"
+
 
 namespace seraph {
 int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, seraph_stats* st);
@@ -173,6 +178,155 @@ int seraph_params_default(seraph_params* p, int algo) {
 int seraph_run(seraph_graph* g, const seraph_params* p, void* out_values, int out_mem,
                seraph_stats* stats) {
     return guarded([&] { return seraph::run_graph(g, p, out_values, out_mem, stats); });
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------ learned scheduler
+
+namespace {
+
+template <class T>
+const T* dev_input(const T* p, uint64_t count, int mem, seraph::DevBuf<T>& hold) {
+    if (mem == SERAPH_MEM_DEVICE) return p;
+    hold.alloc(count ? count : 1);
+    if (count) SR_CUDA(cudaMemcpy(hold.p, p, count * sizeof(T), cudaMemcpyHostToDevice));
+    return hold.p;
+}
+
+uint64_t mix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+extern "C" {
+
+int seraph_sched_create(uint64_t seed, int fp32, seraph_sched_model** out) {
+    return guarded([&] {
+        SR_CHECK(out != nullptr, SERAPH_EINVAL, "out must not be NULL");
+        *out = nullptr;
+        int dev = 0;
+        SR_CUDA(cudaGetDevice(&dev));
+        auto* m = new seraph_sched_model(seed, fp32 != 0);
+        m->device = dev;
+        *out = m;
+        return SERAPH_OK;
+    });
+}
+
+int seraph_sched_get_params(const seraph_sched_model* m, float* params) {
+    return guarded([&] {
+        SR_CHECK(m && params, SERAPH_EINVAL, "null argument");
+        m->model.get_params(params);
+        return SERAPH_OK;
+    });
+}
+
+int seraph_sched_set_params(seraph_sched_model* m, const float* params) {
+    return guarded([&] {
+        SR_CHECK(m && params, SERAPH_EINVAL, "null argument");
+        m->model.set_params(params);
+        return SERAPH_OK;
+    });
+}
+
+int seraph_sched_loss_grad(seraph_sched_model* m, const float* x, const int32_t* k,
+                           const float* prio, uint64_t n, int mem, float* loss, float* grad) {
+    return guarded([&] {
+        SR_CHECK(m && x && k && prio && n > 0, SERAPH_EINVAL, "null argument or n == 0");
+        seraph::DevBuf<float> hx, hp, g(SERAPH_SCHED_PARAMS);
+        seraph::DevBuf<int32_t> hk;
+        const float* dx = dev_input(x, n * SERAPH_SCHED_FEATURES, mem, hx);
+        const int32_t* dk = dev_input(k, n, mem, hk);
+        const float* dp = dev_input(prio, n, mem, hp);
+        const float l = m->model.loss_grad(dx, dk, dp, nullptr, n, g.p, nullptr);
+        if (loss) *loss = l;
+        if (grad) SR_CUDA(cudaMemcpy(grad, g.p, SERAPH_SCHED_PARAMS * sizeof(float), cudaMemcpyDeviceToHost));
+        return SERAPH_OK;
+    });
+}
+
+int seraph_sched_train(seraph_sched_model* m, const float* x, const int32_t* k, const float* prio,
+                       uint64_t n, int mem, uint32_t epochs, uint32_t batch, float lr,
+                       uint64_t seed, float* losses) {
+    return guarded([&] {
+        SR_CHECK(m && x && k && prio && n > 0 && batch > 0, SERAPH_EINVAL, "bad arguments");
+        SR_CHECK(n < (1ull << 32), SERAPH_EINVAL, "too many samples");
+        seraph::DevBuf<float> hx, hp, g(SERAPH_SCHED_PARAMS);
+        seraph::DevBuf<int32_t> hk;
+        const float* dx = dev_input(x, n * SERAPH_SCHED_FEATURES, mem, hx);
+        const int32_t* dk = dev_input(k, n, mem, hk);
+        const float* dp = dev_input(prio, n, mem, hp);
+        std::vector<uint32_t> perm(n);
+        seraph::DevBuf<uint32_t> didx(n);
+        for (uint32_t e = 0; e < epochs; ++e) {
+            for (uint64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
+            for (uint64_t i = n - 1; i > 0; --i) {  // seeded Fisher-Yates shuffle
+                const uint64_t j = mix64(seed, e * n + i) % (i + 1);
+                std::swap(perm[i], perm[j]);
+            }
+            SR_CUDA(cudaMemcpy(didx.p, perm.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice));
+            double sum = 0.0;
+            uint64_t nb = 0;
+            for (uint64_t off = 0; off < n; off += batch, ++nb) {
+                const uint64_t cnt = std::min<uint64_t>(batch, n - off);
+                sum += m->model.loss_grad(dx, dk, dp, didx.p + off, cnt, g.p, nullptr);
+                m->model.adam(g.p, lr, nullptr);
+            }
+            if (losses) losses[e] = (float)(sum / (double)nb);
+        }
+        SR_CUDA(cudaDeviceSynchronize());
+        return SERAPH_OK;
+    });
+}
+
+int seraph_sched_infer(const seraph_sched_model* m, const float* x, uint64_t n, int mem,
+                       int32_t* k_out, float* prio_out) {
+    return guarded([&] {
+        SR_CHECK(m && x && k_out && prio_out, SERAPH_EINVAL, "null argument");
+        if (n == 0) return SERAPH_OK;
+        seraph::DevBuf<float> hx, hp;
+        seraph::DevBuf<int32_t> hk;
+        const float* dx = dev_input(x, n * SERAPH_SCHED_FEATURES, mem, hx);
+        int32_t* dk = k_out;
+        float* dp = prio_out;
+        if (mem != SERAPH_MEM_DEVICE) { hk.alloc(n); hp.alloc(n); dk = hk.p; dp = hp.p; }
+        m->model.infer(dx, n, dk, dp, nullptr);
+        if (mem != SERAPH_MEM_DEVICE) {
+            SR_CUDA(cudaMemcpy(k_out, dk, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            SR_CUDA(cudaMemcpy(prio_out, dp, n * sizeof(float), cudaMemcpyDeviceToHost));
+        }
+        SR_CUDA(cudaDeviceSynchronize());
+        return SERAPH_OK;
+    });
+}
+
+int seraph_sched_targets(const seraph_trace* t, float share, int32_t* k_out, float* prio_out) {
+    return guarded([&] {
+        SR_CHECK(t && k_out && prio_out, SERAPH_EINVAL, "null argument");
+        SR_CHECK(share > 0.f && share <= 1.f, SERAPH_EINVAL, "share must be in (0, 1]");
+        for (uint64_t r = 0; r < t->count; ++r) {
+            const uint32_t* g = t->gains + r * SERAPH_SCHED_FEATURES;
+            double total = 0.0;
+            for (int j = 0; j < 16; ++j) total += g[j];
+            int k = 1;
+            double acc = g[0];
+            while (k < 16 && acc < share * total) acc += g[k++];
+            k_out[r] = k;
+            prio_out[r] = (float)(std::log2(1.0 + g[0]) / 24.0);
+        }
+        return SERAPH_OK;
+    });
+}
+
+void seraph_sched_free(seraph_sched_model* m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    delete m;
 }
 
 }  // extern "C"

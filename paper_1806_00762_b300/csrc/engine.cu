@@ -336,11 +336,14 @@ __device__ __forceinline__ void flush_locals(const AlgoArgs& a, int par, uint32_
 // ---------------------------------------------------------------- kernels
 
 __global__ void gate_kernel(RunState* rs, uint32_t pass, int check_prev, int idle,
-                            uint32_t want_loaded) {
+                            uint32_t want_loaded, uint32_t j, int learned, unsigned* rec_gains) {
     const int par = pass & 1;
+    if (rec_gains && j > 0) rec_gains[j - 1] = rs->pass_changed[par ^ 1];
     bool go = true;
     if (check_prev && rs->pass_changed[par ^ 1] == 0) go = false;
     if (idle && (int)(*(volatile unsigned*)&rs->loaded - want_loaded) >= 0) go = false;
+    if (learned && j >= rs->k_limit) go = false;
+    if (go) rs->step_passes += 1;
     rs->pass_go[par] = go;
     for (int k = 0; k < 8; ++k) rs->work[par][k] = 0;
     rs->pass_changed[par] = 0;
@@ -547,9 +550,25 @@ __global__ void init_pr_kernel(const uint32_t* outdeg, float* x, float* contrib,
     }
 }
 
+__global__ void step_epilogue_kernel(RunState* rs, ChunkDyn* cd, uint32_t chunk,
+                                     uint32_t last_pass, uint32_t npass, unsigned* rec_gains) {
+    const unsigned last = rs->pass_changed[last_pass & 1];
+    if (rec_gains && npass > 0) rec_gains[npass - 1] = last;
+    if (cd) {
+        ChunkDyn d = cd[chunk];
+        d.visits += 1;
+        d.last_passes = rs->step_passes;
+        for (int k = 0; k < 4; ++k) d.gains[k] = 0;
+        if (rec_gains)
+            for (uint32_t k = 0; k < 4 && k < npass; ++k) d.gains[k] = rec_gains[k];
+        cd[chunk] = d;
+    }
+}
+
 __global__ void close_min_kernel(RunState* rs, SweepReport* out) {
     SweepReport r = rs->cur;
     r.thr_min = rs->thr_cur;
+    rs->prev_changed = r.changed;
     *out = r;
     rs->thr_prev = rs->thr_cur;
     rs->thr_cur = SERAPH_INF;
@@ -606,6 +625,7 @@ __global__ void __launch_bounds__(kNT) pr_close_final_kernel(RunState* rs, const
         rs->base = (float)((1.0 - damping) / (double)n + damping * D / (double)n);
         if (out) {
             SweepReport rep = rs->cur;
+            rs->prev_changed = rep.changed;
             rep.resid = r;
             rep.dangling = D;
             rep.thr_min = rs->thr_cur;
@@ -624,8 +644,14 @@ unsigned grid_1d(uint64_t n) {
 }  // namespace
 
 void launch_gate(RunState* rs, uint32_t pass, int check_prev, int idle, uint32_t want_loaded,
-                 cudaStream_t s) {
-    gate_kernel<<<1, 1, 0, s>>>(rs, pass, check_prev, idle, want_loaded);
+                 uint32_t j, int learned, unsigned* rec_gains, cudaStream_t s) {
+    gate_kernel<<<1, 1, 0, s>>>(rs, pass, check_prev, idle, want_loaded, j, learned, rec_gains);
+    SR_LAUNCH();
+}
+
+void launch_step_epilogue(RunState* rs, ChunkDyn* cd, uint32_t chunk, uint32_t last_pass,
+                          uint32_t npass, unsigned* rec_gains, cudaStream_t s) {
+    step_epilogue_kernel<<<1, 1, 0, s>>>(rs, cd, chunk, last_pass, npass, rec_gains);
     SR_LAUNCH();
 }
 

@@ -46,7 +46,10 @@ struct RunState {
     SweepReport cur;
     unsigned int pass_go[2];      // pass decision of the gate kernel
     unsigned int loaded;          // sequence number of the last chunk load done
+    unsigned int k_limit;         // learned schedule: passes allowed in this step
+    unsigned int step_passes;     // passes run in the current step
     unsigned int pad1;
+    unsigned long long prev_changed;  // changes of the previous sweep
     unsigned int pass_changed[2];
     unsigned int list_cnt[2][8];
     unsigned int work[2][8];
@@ -56,6 +59,14 @@ struct RunState {
 };
 
 enum { ALG_SSSP = 0, ALG_BFS = 1, ALG_CC = 2, ALG_PR = 3 };
+
+// Per-chunk inputs of the learned scheduler's features.
+struct ChunkStatic {
+    float nv, ne, maxdeg, bytes_frac;  // vertices, in-edges, max in-degree, bytes / slot
+};
+struct ChunkDyn {
+    unsigned visits, last_passes, gains[4];  // visits so far; passes and first 4 pass gains of the last visit
+};
 
 struct AlgoArgs {
     uint32_t* val;            // SSSP/BFS/CC values
@@ -87,7 +98,10 @@ struct AlgoArgs {
 // idle-slot pass is only worth running while the copy is in flight).
 // `predict` = 0 runs the pass with prediction off.
 void launch_gate(RunState* rs, uint32_t pass, int check_prev, int idle, uint32_t want_loaded,
-                 cudaStream_t s);
+                 uint32_t j, int learned, unsigned* rec_gains, cudaStream_t s);
+// After the last pass of a step: record its gain, update the chunk's state.
+void launch_step_epilogue(RunState* rs, ChunkDyn* cd, uint32_t chunk, uint32_t last_pass,
+                          uint32_t npass, unsigned* rec_gains, cudaStream_t s);
 void launch_compact(int algo, const WindowDesc& wd, const AlgoArgs& a, uint32_t pass,
                     int predict, cudaStream_t s);
 void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, uint32_t step,

@@ -21,6 +21,7 @@ struct PageMeta {
     uint64_t off_bytes; // bytes of the padded offset array
     uint64_t w_off;     // byte offset in the weight region
     uint64_t w_bytes;   // weight bytes (ne * weight width, padded), 0 if unweighted
+    uint32_t maxdeg;    // largest in-degree in the page
 };
 
 struct seraph_graph {

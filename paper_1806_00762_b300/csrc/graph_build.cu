@@ -388,7 +388,8 @@ __global__ void gather_off_kernel(const uint64_t* __restrict__ col_off,
 // Page-relative offsets: stage[st[p] + i] = off[vb_p + i] - off[vb_p], i in [0, nv_p].
 __global__ void stage_off_kernel(const uint64_t* __restrict__ col_off,
                                  const uint64_t* __restrict__ vb, const uint64_t* __restrict__ st,
-                                 uint32_t P, uint64_t n, uint32_t* __restrict__ stage) {
+                                 uint32_t P, uint64_t n, uint32_t* __restrict__ stage,
+                                 unsigned* __restrict__ page_maxdeg) {
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v <= n;
          v += (uint64_t)gridDim.x * blockDim.x) {
         // page p owning v: largest p with vb[p] <= v, p < P (v = n closes page P-1)
@@ -399,6 +400,10 @@ __global__ void stage_off_kernel(const uint64_t* __restrict__ col_off,
         }
         uint32_t p = lo;
         stage[st[p] + (v - vb[p])] = (uint32_t)(col_off[v] - col_off[vb[p]]);
+        if (v < n) {
+            const uint64_t d = col_off[v + 1] - col_off[v];
+            if (d) atomicMax(&page_maxdeg[p], d > 0xFFFFFFFFull ? 0xFFFFFFFFu : (unsigned)d);
+        }
         // a vertex that closes page p-1 (v == vb[p], p > 0) also writes its end
         if (v == vb[p] && p > 0) {
             uint32_t q = p - 1;
@@ -599,9 +604,17 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
 
     DevBuf<uint64_t> d_st(P + 1);
     DevBuf<uint32_t> stage(stage_n);
+    DevBuf<unsigned> pmax(P);
     SR_CUDA(cudaMemcpyAsync(d_st.p, st.data(), (P + 1) * 8, cudaMemcpyHostToDevice, s));
-    stage_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(col_off.p, d_vb.p, d_st.p, P, n, stage.p);
+    SR_CUDA(cudaMemsetAsync(pmax.p, 0, P * sizeof(unsigned), s));
+    stage_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(col_off.p, d_vb.p, d_st.p, P, n, stage.p, pmax.p);
     SR_LAUNCH();
+    {
+        std::vector<unsigned> hmax(P);
+        SR_CUDA(cudaMemcpyAsync(hmax.data(), pmax.p, P * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        SR_CUDA(cudaStreamSynchronize(s));
+        for (uint32_t p = 0; p < P; ++p) g->pages[p].maxdeg = hmax[p];
+    }
 
     g->h_struct.alloc(s_off);
     if (weighted) g->h_weight.alloc(w_off);

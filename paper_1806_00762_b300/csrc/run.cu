@@ -26,8 +26,12 @@
 #include <thread>
 #include <vector>
 
+#include <algorithm>
+#include <numeric>
+
 #include "engine.cuh"
 #include "graph.hpp"
+#include "mlp.cuh"
 
 namespace seraph {
 namespace {
@@ -72,6 +76,20 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 // loads and evictions.
 class Schedule {
   public:
+    // Dynamic schedule (window of one chunk, a chunk order chosen per sweep).
+    explicit Schedule(uint32_t C) : C_(C), W_(1), zigzag_(false), dynamic_(true) {
+        for (uint32_t c = 0; c < C; ++c) singles_.push_back({c});
+        std::vector<uint32_t> first(C);
+        std::iota(first.begin(), first.end(), 0u);
+        orders_.push_back(first);
+        starts_.push_back(0);
+    }
+    // The next sweep's order (appended after the last known sweep).
+    void append_order(const std::vector<uint32_t>& order) {
+        starts_.push_back(starts_.back() + orders_.back().size());
+        orders_.push_back(order);
+    }
+
     Schedule(uint32_t C, uint32_t W, int order, bool resident)
         : C_(C), W_(resident ? (W < C ? W : C) : W), zigzag_(!resident && order == SERAPH_ORDER_ZIGZAG) {
         if (!zigzag_) {  // sliding window, cyclic over the chunks
@@ -103,10 +121,22 @@ class Schedule {
     }
 
     const std::vector<uint32_t>& window(uint64_t t) const {
+        if (dynamic_) {
+            size_t j;
+            uint64_t i;
+            locate(t, j, i);
+            return singles_[orders_[j][i]];
+        }
         return table_[t < ramp_ ? t : ramp_ + (t - ramp_) % period_];
     }
 
     bool sweep_end(uint64_t t) const {
+        if (dynamic_) {
+            size_t j;
+            uint64_t i;
+            locate(t, j, i);
+            return i + 1 == orders_[j].size();
+        }
         if (!zigzag_) return t % C_ == C_ - 1;
         if (t < ramp_) return false;
         const uint64_t u = t - ramp_, span = C_ - W_;
@@ -114,10 +144,19 @@ class Schedule {
     }
 
   private:
+    // sweep j and position i of step t; beyond the known sweeps the last
+    // order is assumed to repeat (look-ahead only)
+    void locate(uint64_t t, size_t& j, uint64_t& i) const {
+        j = (size_t)(std::upper_bound(starts_.begin(), starts_.end(), t) - starts_.begin()) - 1;
+        i = t - starts_[j];
+        if (j + 1 == orders_.size() && i >= orders_[j].size()) i %= orders_[j].size();
+    }
     uint32_t C_, W_;
-    bool zigzag_;
+    bool zigzag_, dynamic_ = false;
     uint64_t ramp_ = 0, period_ = 1;
     std::vector<std::vector<uint32_t>> table_;
+    std::vector<std::vector<uint32_t>> orders_, singles_;
+    std::vector<uint64_t> starts_;
 };
 
 }  // namespace
@@ -143,6 +182,13 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CHECK(P->thread_max_deg <= P->group4_max_deg && P->group4_max_deg <= P->group8_max_deg &&
                  P->group8_max_deg <= P->warp_max_deg,
              SERAPH_EINVAL, "need thread_max_deg <= group4_max_deg <= group8_max_deg <= warp_max_deg");
+    const bool learned = P->sched == SERAPH_SCHED_LEARNED;
+    seraph_trace* trace = (seraph_trace*)P->trace;
+    SR_CHECK(P->sched == SERAPH_SCHED_FIXED || learned, SERAPH_EINVAL, "bad sched");
+    SR_CHECK(!learned || P->sched_model, SERAPH_EINVAL, "learned schedule needs sched_model");
+    SR_CHECK(!(learned || trace) || P->window == 1, SERAPH_EINVAL,
+             "learned schedules and traces need window = 1");
+    const SchedModel* model = learned ? &((seraph_sched_model*)P->sched_model)->model : nullptr;
     const uint64_t n = g->n;
     int algo = P->algo;
     if ((algo == SERAPH_SSSP || algo == SERAPH_BFS))
@@ -290,7 +336,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     ev_stop.create(true);
     ev_sweep.create(false);
     const bool prof = P->profile != 0;
-    const uint32_t max_passes = std::max(P->max_passes, P->passes);
+    // a learned step may run up to 16 passes unless max_passes says otherwise
+    const uint32_t max_passes =
+        learned && P->max_passes <= P->passes ? 16u : std::max(P->max_passes, P->passes);
     // profiling pools, indexed by step within the ring
     std::vector<Event> pc_b, pc_e, pk_b, pk_e, pr_b, pr_e;
     if (prof) {
@@ -313,8 +361,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     std::vector<int64_t> last_use(nslots, -1);   // slot -> last step that used it
     std::vector<uint8_t> pending(C, 0);          // copied but not yet waited on by compute
     uint32_t load_seq = 0, loads_timed = 0;
-    Schedule sched(C, W, (int)P->order, resident);
-    const bool zig = !resident && P->order == SERAPH_ORDER_ZIGZAG;
+    Schedule sched = learned ? Schedule(C) : Schedule(C, W, (int)P->order, resident);
+    const bool zig = !learned && !resident && P->order == SERAPH_ORDER_ZIGZAG;
 
     // Look-ahead over the deterministic window sequence: next step >= from
     // whose window holds chunk c (or `horizon` if none within it).
@@ -408,6 +456,54 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     };
 
     const unsigned relax_grid = device_sms() * 8;
+    // learned scheduler / trace state
+    const bool track = learned || trace;
+    DevBuf<ChunkStatic> d_cs;
+    DevBuf<ChunkDyn> d_cd;
+    DevBuf<float> rec_feat, d_feats, d_prio;
+    DevBuf<unsigned> rec_gain;
+    DevBuf<int32_t> d_kp;
+    PinnedBuf h_feat, h_gain, h_prio;
+    const uint32_t rec_rows = C + W + 2;
+    if (track) {
+        std::vector<ChunkStatic> cs_h(C);
+        for (uint32_t c = 0; c < C; ++c) {
+            ChunkStatic x{};
+            x.nv = (float)(chunks[c].v_end - chunks[c].v_begin);
+            float ne = 0.f, md = 0.f;
+            for (uint32_t p = chunks[c].first_page; p < chunks[c].end_page; ++p) {
+                ne += (float)g->pages[p].ne;
+                md = std::max(md, (float)g->pages[p].maxdeg);
+            }
+            x.ne = ne;
+            x.maxdeg = md;
+            x.bytes_frac = (float)(chunks[c].s_bytes + (use_w ? chunks[c].w_bytes : 0)) / (float)slot_bytes;
+            cs_h[c] = x;
+        }
+        d_cs.alloc(C);
+        d_cd.alloc(C);
+        SR_CUDA(cudaMemcpy(d_cs.p, cs_h.data(), C * sizeof(ChunkStatic), cudaMemcpyHostToDevice));
+        SR_CUDA(cudaMemset(d_cd.p, 0, C * sizeof(ChunkDyn)));
+        rec_feat.alloc((uint64_t)rec_rows * kSchedIn);
+        rec_gain.alloc((uint64_t)rec_rows * 16);
+        SR_CUDA(cudaMemset(rec_gain.p, 0, (uint64_t)rec_rows * 16 * sizeof(unsigned)));
+        h_feat.alloc((uint64_t)rec_rows * kSchedIn * sizeof(float));
+        h_gain.alloc((uint64_t)rec_rows * 16 * sizeof(unsigned));
+        if (learned) {
+            d_feats.alloc((uint64_t)C * kSchedIn);
+            d_prio.alloc(C);
+            d_kp.alloc(C);
+            h_prio.alloc(C * sizeof(float));
+        }
+        if (trace) trace->count = 0;
+    }
+    SchedArgs sa{};
+    sa.cs = d_cs.p;
+    sa.cd = d_cd.p;
+    sa.rs = rs.p;
+    sa.inv_n = (float)(1.0 / (double)n);
+    sa.is_pr = is_pr ? 1.f : 0.f;
+    uint32_t skip_streak = 0;  // consecutive learned sweeps that skipped chunks
     uint32_t pass = 0;
     bool predict = P->pvu != SERAPH_PVU_OFF;
     bool pr_predict_off = false;
@@ -473,10 +569,20 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             wd.nblocks = blocks;
         }
         const bool pred_now = is_pr ? (predict && !pr_predict_off) : predict;
-        npass = max_passes > P->passes && (prefetch || resident) ? max_passes : P->passes;
+        npass = max_passes > P->passes && (prefetch || resident || learned) ? max_passes : P->passes;
+        const uint64_t row = t - sweep_first_step;
+        unsigned* rec_row = track && row < rec_rows ? rec_gain.p + row * 16 : nullptr;
+        if (track) {
+            sa.predict = pred_now ? 1.f : 0.f;
+            sa.sweep = (float)S.sweeps;
+            launch_sched_step(sa, rs.p, win[0], rec_row ? rec_feat.p + row * kSchedIn : nullptr,
+                              learned ? model : nullptr, cs.s);
+            ++launches;
+        }
         for (uint32_t j = 0; j < npass; ++j) {
-            const bool idle = j >= P->passes;
-            launch_gate(rs.p, pass, j > 0, idle && prefetch, want, cs.s);
+            const bool idle = j >= P->passes && !learned;
+            launch_gate(rs.p, pass, j > 0, idle && prefetch, want, j, learned ? 1 : 0,
+                        j < 16 ? rec_row : nullptr, cs.s);
             launch_compact(algo, wd, a, pass, pred_now ? 1 : 0, cs.s);
             if (prof) SR_CUDA(cudaEventRecord(pr_b[(t % ring) * max_passes + j].e, cs.s));
             launch_relax(algo, P->kahan, a, pass, (uint32_t)t, relax_grid, cs.s);
@@ -488,6 +594,10 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
                 ++launches;
             }
             ++pass;
+        }
+        if (track) {
+            launch_step_epilogue(rs.p, d_cd.p, win[0], pass - 1, std::min<uint32_t>(npass, 16), rec_row, cs.s);
+            ++launches;
         }
         if (prof) SR_CUDA(cudaEventRecord(pk_e[t % ring].e, cs.s));
         SR_CUDA(cudaEventRecord(step_done[t % ring].e, cs.s));
@@ -506,6 +616,20 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         launches += is_pr ? 2 : 1;
         SR_CUDA(cudaMemcpyAsync(h_rep.p, d_rep.p, sizeof(SweepReport), cudaMemcpyDeviceToHost, cs.s));
         SR_CUDA(cudaMemcpyAsync(h_steps.p, d_steps.p, ring * sizeof(unsigned), cudaMemcpyDeviceToHost, cs.s));
+        const uint64_t rows_now = std::min<uint64_t>(t + 1 - sweep_first_step, rec_rows);
+        if (trace) {
+            SR_CUDA(cudaMemcpyAsync(h_feat.p, rec_feat.p, rows_now * kSchedIn * sizeof(float), cudaMemcpyDeviceToHost, cs.s));
+            SR_CUDA(cudaMemcpyAsync(h_gain.p, rec_gain.p, rows_now * 16 * sizeof(unsigned), cudaMemcpyDeviceToHost, cs.s));
+        }
+        if (learned) {
+            sa.predict = predict ? 1.f : 0.f;
+            sa.sweep = (float)(S.sweeps + 1);
+            launch_sched_features(sa, C, d_feats.p, cs.s);
+            model->infer(d_feats.p, C, d_kp.p, d_prio.p, cs.s);
+            SR_CUDA(cudaMemcpyAsync(h_prio.p, d_prio.p, C * sizeof(float), cudaMemcpyDeviceToHost, cs.s));
+            launches += 2;
+        }
+        if (track) SR_CUDA(cudaMemsetAsync(rec_gain.p, 0, (uint64_t)rec_rows * 16 * sizeof(unsigned), cs.s));
         SR_CUDA(cudaEventRecord(ev_sweep.e, cs.s));
         wait_event(ev_sweep.e, P->timeout_ms);
         SweepReport rep;
@@ -544,6 +668,16 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
                 S.copy_ms += elapsed(pc_b[loads_timed % ring].e, pc_e[loads_timed % ring].e);
             }
         }
+        if (trace) {
+            for (uint64_t r = 0; r < rows_now && trace->count < trace->capacity; ++r) {
+                const uint64_t o = trace->count++;
+                std::memcpy(trace->features + o * kSchedIn, (const float*)h_feat.p + r * kSchedIn,
+                            kSchedIn * sizeof(float));
+                std::memcpy(trace->gains + o * 16, (const unsigned*)h_gain.p + r * 16, 16 * sizeof(unsigned));
+                const Chunk& ch = chunks[sched.window(sweep_first_step + r)[0]];
+                if (trace->vertices) trace->vertices[o] = ch.v_end - ch.v_begin;
+            }
+        }
         sweep_first_step = t + 1;
         bool stop = false;
         if (is_pr) {
@@ -566,6 +700,24 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             if (!stop && S.sweeps >= P->max_sweeps) { rc = SERAPH_ENOTCONV; stop = true; }
         }
         if (stop) break;
+        if (learned) {  // the next sweep streams chunks in descending predicted priority
+            const float* pr = (const float*)h_prio.p;
+            std::vector<uint32_t> ord(C);
+            std::iota(ord.begin(), ord.end(), 0u);
+            std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return pr[x] > pr[y]; });
+            // SSSP/BFS/CC: skip chunks predicted to change nothing, except after
+            // a sweep without changes and at least every fourth sweep (the
+            // stop rule needs every chunk processed after the last change)
+            const bool may_skip = !is_pr && rep.changed > 0 && skip_streak < 3;
+            if (may_skip) {
+                std::vector<uint32_t> keep;
+                for (uint32_t c : ord)
+                    if (pr[c] >= 0.02f) keep.push_back(c);
+                if (!keep.empty() && keep.size() < C) ord.swap(keep);
+            }
+            skip_streak = ord.size() < C ? skip_streak + 1 : 0;
+            sched.append_order(ord);
+        }
     }
     SR_CUDA(cudaEventRecord(ev_stop.e, cs.s));
     SR_CUDA(cudaStreamSynchronize(cs.s));

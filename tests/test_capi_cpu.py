@@ -85,3 +85,17 @@ def test_input_module_and_oracle_libraries_load():
     synth._dev_lib()
     oracle._L()
     assert hasattr(synth._dev_lib(), "synth_rmat_device")
+
+
+def test_sched_targets_on_a_handmade_trace():
+    """k = smallest number of passes holding >= share of the step's changes;
+    priority = log2(1 + first-pass changes) / 24 (host code, no GPU)."""
+    import numpy as np
+    tr = seraph.TraceBuffer(3)
+    tr.gains[0, :4] = [100, 10, 0, 0]     # 110 total: 100/110 < .95 -> k = 2
+    tr.gains[1, :3] = [0, 0, 0]           # no change: k = 1
+    tr.gains[2, :16] = 1                  # uniform: need 16 * .95 -> 16
+    tr.struct.count = 3
+    k, prio = tr.targets(0.95)
+    assert list(k) == [2, 1, 16]
+    assert abs(prio[0] - np.log2(101) / 24) < 1e-6 and prio[1] == 0.0

@@ -1,0 +1,142 @@
+"""Learned scheduler: network kernels against the FP64 reference, trace
+collection, training, and the learned schedule's results (bit-exact for
+SSSP/BFS/CC, within tolerance for PageRank)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1806_00762_b300 as seraph
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(n=300, seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.random((n, 16)).astype(np.float32)
+    k = rng.integers(1, 17, n).astype(np.int32)
+    prio = rng.random(n).astype(np.float32)
+    return x, k, prio
+
+
+def _close(got, ref, rtol):
+    err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert err <= rtol, err
+
+
+def test_fp32_gradient_matches_oracle():
+    m = seraph.SchedModel(seed=7, fp32=True)
+    x, k, prio = _batch()
+    loss, g = m.loss_grad(x, k, prio)
+    rl, rg = mlp.loss_grad(m.get_params().astype(np.float64), x, k, prio)
+    assert abs(loss - rl) <= 1e-5 * abs(rl)
+    _close(g, rg, 1e-5)
+
+
+def test_bf16_gradient_matches_oracle_with_rounded_weights():
+    m = seraph.SchedModel(seed=3, fp32=False)
+    x, k, prio = _batch(seed=1)
+    loss, g = m.loss_grad(x, k, prio)
+    w = mlp.bf16_round(m.get_params()).astype(np.float64)
+    rl, rg = mlp.loss_grad(w, x, k, prio)
+    assert abs(loss - rl) <= 1e-4 * abs(rl)
+    _close(g, rg, 1e-4)
+    # against unrounded FP64 weights the BF16 forward stays within 1e-2
+    _, rg_full = mlp.loss_grad(m.get_params().astype(np.float64), x, k, prio)
+    _close(g, rg_full, 1e-2)
+
+
+def test_inference_matches_oracle():
+    m = seraph.SchedModel(seed=11)
+    x, _, _ = _batch(1000, seed=2)
+    k, prio = m.infer(x)
+    o, _ = mlp.forward(mlp.bf16_round(m.get_params()).astype(np.float64), x)
+    kr = np.argmax(o[:, :16], axis=1) + 1
+    top2 = np.sort(o[:, :16], axis=1)[:, -2:]
+    clear = (top2[:, 1] - top2[:, 0]) > 1e-4      # ignore near-ties
+    assert np.array_equal(k[clear], kr[clear])
+    assert np.allclose(prio, o[:, 16], atol=1e-4)
+
+
+def test_training_reduces_loss_and_learns_a_rule():
+    rng = np.random.default_rng(5)
+    x = rng.random((4096, 16)).astype(np.float32)
+    k = (1 + np.floor(x[:, 0] * 4)).astype(np.int32) * 2          # 2, 4, 6, 8
+    prio = (0.5 * x[:, 1] + 0.25 * x[:, 2]).astype(np.float32)
+    m = seraph.SchedModel(seed=1)
+    losses = m.train(x, k, prio, epochs=40, batch=256, lr=3e-3, seed=2)
+    assert losses[-1] < 0.25 * losses[0]
+    kp, pp = m.infer(x)
+    assert np.mean(kp == k) > 0.85
+    assert np.mean(np.abs(pp - prio)) < 0.05
+
+
+@pytest.fixture(scope="module")
+def r13():
+    n = 1 << 13
+    src, dst = synth.rmat_edges(13)
+    w = synth.weights(src, dst)
+    og = oracle.build_csr(n, src, dst, w)
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=48)
+    gs = seraph.Graph.from_edges(n, src, dst, None, symmetrize=True, num_pages=48)
+    return dict(n=n, g=g, gs=gs, og=og, sssp=oracle.sssp(og, 5), bfs=oracle.bfs(og, 5),
+                cc=oracle.cc(og), pr=oracle.pagerank(og)[0])
+
+
+def _budget(g, slots, per_slot=1.7, use_w=True):
+    i = g.info()
+    slot = (i["max_page_struct_bytes"] + 255) // 256 * 256 + (i["max_page_weight_bytes"] if use_w else 0)
+    return int(slots * slot * per_slot) + 256 * slots
+
+
+def test_trace_rows_account_for_every_change(r13):
+    tr = seraph.TraceBuffer(4096)
+    d, st = seraph.run(r13["g"], "sssp", source=5, window=1, slots=6, passes=16, trace=tr,
+                       budget_bytes=_budget(r13["g"], 6))
+    assert np.array_equal(d, r13["sssp"])
+    f, gains, nv = tr.rows()
+    assert tr.count == st["steps"]
+    assert int(gains.sum()) == st["changes"]
+    assert np.all(f >= 0) and np.all(f <= 1.0 + 1e-6)
+    assert np.all(nv > 0)
+    k, prio = tr.targets(0.95)
+    assert k.min() >= 1 and k.max() <= 16 and np.all(prio >= 0)
+
+
+@pytest.fixture(scope="module")
+def trained(r13):
+    """A model trained on SSSP and PageRank traces of the fixed pipeline."""
+    xs, ks, ps = [], [], []
+    for algo, g in (("sssp", r13["g"]), ("pagerank", r13["g"]), ("bfs", r13["g"])):
+        tr = seraph.TraceBuffer(20000)
+        seraph.run(g, algo, source=5, window=1, slots=6, passes=16, trace=tr,
+                   budget_bytes=_budget(g, 6, use_w=algo == "sssp"))
+        f, _, _ = tr.rows()
+        k, p = tr.targets(0.95)
+        xs.append(f.copy()); ks.append(k); ps.append(p)
+    m = seraph.SchedModel(seed=4)
+    losses = m.train(np.concatenate(xs), np.concatenate(ks), np.concatenate(ps), epochs=30,
+                     batch=128, lr=2e-3)
+    assert losses[-1] < losses[0]
+    return m
+
+
+@pytest.mark.parametrize("which", ["trained", "untrained"])
+@pytest.mark.parametrize("algo", ["sssp", "bfs", "cc", "pagerank"])
+def test_learned_schedule_results(r13, trained, which, algo):
+    model = trained if which == "trained" else seraph.SchedModel(seed=99)
+    g = r13["gs"] if algo == "cc" else r13["g"]
+    got, st = seraph.run(g, algo, source=5, window=1, slots=6, sched_model=model,
+                         budget_bytes=_budget(g, 6, use_w=algo == "sssp"))
+    assert st["converged"] == 1
+    if algo == "pagerank":
+        err = np.abs(got.astype(np.float64) - r13["pr"])
+        assert err.sum() <= 1e-5 and np.max(err / r13["pr"]) <= 1e-4
+    else:
+        assert np.array_equal(got, r13[algo])
+
+
+def test_learned_schedule_needs_window_one(r13, trained):
+    with pytest.raises(seraph.SeraphError, match="EINVAL"):
+        seraph.run(r13["g"], "sssp", window=2, sched_model=trained)
