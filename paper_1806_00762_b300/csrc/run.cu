@@ -76,8 +76,10 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 // loads and evictions.
 class Schedule {
   public:
-    // Dynamic schedule (window of one chunk, a chunk order chosen per sweep).
-    explicit Schedule(uint32_t C) : C_(C), W_(1), zigzag_(false), dynamic_(true) {
+    // Dynamic schedule (window of one chunk, a chunk order chosen per sweep;
+    // sweeps not chosen yet are assumed to visit every chunk, alternating
+    // direction when `zig`).
+    Schedule(uint32_t C, bool zig) : C_(C), W_(1), zigzag_(zig), dynamic_(true) {
         for (uint32_t c = 0; c < C; ++c) singles_.push_back({c});
         std::vector<uint32_t> first(C);
         std::iota(first.begin(), first.end(), 0u);
@@ -122,20 +124,17 @@ class Schedule {
 
     const std::vector<uint32_t>& window(uint64_t t) const {
         if (dynamic_) {
-            size_t j;
-            uint64_t i;
-            locate(t, j, i);
-            return singles_[orders_[j][i]];
+            bool end;
+            return singles_[dyn_chunk(t, &end)];
         }
         return table_[t < ramp_ ? t : ramp_ + (t - ramp_) % period_];
     }
 
     bool sweep_end(uint64_t t) const {
         if (dynamic_) {
-            size_t j;
-            uint64_t i;
-            locate(t, j, i);
-            return i + 1 == orders_[j].size();
+            bool end;
+            dyn_chunk(t, &end);
+            return end;
         }
         if (!zigzag_) return t % C_ == C_ - 1;
         if (t < ramp_) return false;
@@ -146,10 +145,19 @@ class Schedule {
   private:
     // sweep j and position i of step t; beyond the known sweeps the last
     // order is assumed to repeat (look-ahead only)
-    void locate(uint64_t t, size_t& j, uint64_t& i) const {
-        j = (size_t)(std::upper_bound(starts_.begin(), starts_.end(), t) - starts_.begin()) - 1;
-        i = t - starts_[j];
-        if (j + 1 == orders_.size() && i >= orders_[j].size()) i %= orders_[j].size();
+    // Chunk and end-of-sweep flag of dynamic step t.
+    uint32_t dyn_chunk(uint64_t t, bool* end) const {
+        size_t j = (size_t)(std::upper_bound(starts_.begin(), starts_.end(), t) - starts_.begin()) - 1;
+        uint64_t i = t - starts_[j];
+        if (i < orders_[j].size()) {
+            *end = i + 1 == orders_[j].size();
+            return orders_[j][i];
+        }
+        // beyond the known sweeps: full sweeps in the base direction
+        const uint64_t off = i - orders_[j].size();
+        const uint64_t js = orders_.size() + off / C_, k = off % C_;
+        *end = k + 1 == C_;
+        return (uint32_t)(zigzag_ && (js & 1) ? C_ - 1 - k : k);
     }
     uint32_t C_, W_;
     bool zigzag_, dynamic_ = false;
@@ -338,7 +346,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     const bool prof = P->profile != 0;
     // a learned step may run up to 16 passes unless max_passes says otherwise
     const uint32_t max_passes =
-        learned && P->max_passes <= P->passes ? 16u : std::max(P->max_passes, P->passes);
+        learned && P->max_passes == 0 ? 16u : std::max(P->max_passes, P->passes);
     // profiling pools, indexed by step within the ring
     std::vector<Event> pc_b, pc_e, pk_b, pk_e, pr_b, pr_e;
     if (prof) {
@@ -361,8 +369,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     std::vector<int64_t> last_use(nslots, -1);   // slot -> last step that used it
     std::vector<uint8_t> pending(C, 0);          // copied but not yet waited on by compute
     uint32_t load_seq = 0, loads_timed = 0;
-    Schedule sched = learned ? Schedule(C) : Schedule(C, W, (int)P->order, resident);
-    const bool zig = !learned && !resident && P->order == SERAPH_ORDER_ZIGZAG;
+    const bool zig_base = !resident && P->order == SERAPH_ORDER_ZIGZAG;
+    Schedule sched = learned ? Schedule(C, zig_base) : Schedule(C, W, (int)P->order, resident);
+    const bool zig = zig_base;
 
     // Look-ahead over the deterministic window sequence: next step >= from
     // whose window holds chunk c (or `horizon` if none within it).
@@ -700,11 +709,11 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             if (!stop && S.sweeps >= P->max_sweeps) { rc = SERAPH_ENOTCONV; stop = true; }
         }
         if (stop) break;
-        if (learned) {  // the next sweep streams chunks in descending predicted priority
+        if (learned) {  // the next sweep: the base order without chunks predicted idle
             const float* pr = (const float*)h_prio.p;
             std::vector<uint32_t> ord(C);
             std::iota(ord.begin(), ord.end(), 0u);
-            std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return pr[x] > pr[y]; });
+            if (zig_base && (S.sweeps & 1)) std::reverse(ord.begin(), ord.end());
             // SSSP/BFS/CC: skip chunks predicted to change nothing, except after
             // a sweep without changes and at least every fourth sweep (the
             // stop rule needs every chunk processed after the last change)

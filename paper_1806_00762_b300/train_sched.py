@@ -1,0 +1,111 @@
+"""Train the learned scheduler on traces of the fixed pipeline.
+
+Traces come from SSSP, BFS and PageRank runs on seeded R-MAT graphs (scale
+24 with small ring slots, and scale 28 with the benchmark's ring), each step
+running up to 16 local passes so that the gain of every extra pass is seen.
+Targets (seraph_sched_targets): k = fewest passes holding 95 % of a step's
+changes, priority = log2(1 + first-pass changes) / 24.  Training uses the
+library's own forward/backward/Adam kernels.  The FP32 master weights are
+written as raw little-endian float32 (6353 values), with a JSON summary.
+
+    python -m paper_1806_00762_b300.train_sched --out paper_1806_00762_b300/sched_weights.f32
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+DEFAULT_WEIGHTS = os.path.join(HERE, "sched_weights.f32")
+
+
+def _graph(seraph, synth, torch, scale, pages):
+    n = 1 << scale
+    m = synth.rmat_config(scale).m
+    src = torch.empty(m, dtype=torch.int32, device="cuda")
+    dst = torch.empty_like(src)
+    w = torch.empty_like(src)
+    synth.rmat_edges_device(scale, src.data_ptr(), dst.data_ptr(), w.data_ptr())
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=pages)
+    del src, dst, w
+    torch.cuda.empty_cache()
+    return g
+
+
+def collect(seraph, torch, g, budget, slots, runs):
+    xs, ks, ps = [], [], []
+    n = g.info()["n"]
+    for algo, source in runs:
+        tr = seraph.TraceBuffer(500_000)
+        out = torch.empty(n, dtype=torch.float32 if algo == "pagerank" else torch.int32,
+                          device="cuda")
+        seraph.run(g, algo, out=out, source=source, window=1, slots=slots, passes=16, trace=tr,
+                   budget_bytes=budget)
+        f, _, _ = tr.rows()
+        k, p = tr.targets(0.95)
+        xs.append(f.copy())
+        ks.append(k)
+        ps.append(p)
+    return xs, ks, ps
+
+
+def load(path: str = DEFAULT_WEIGHTS):
+    """Parameters saved by this script, or None if the file is absent."""
+    if not os.path.exists(path):
+        return None
+    return np.fromfile(path, dtype="<f4")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--scales", default="24,28")
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--seed", type=int, default=1)
+    args = ap.parse_args()
+    import torch
+    import synth
+    import paper_1806_00762_b300 as seraph
+
+    t0 = time.time()
+    xs, ks, ps = [], [], []
+    for scale in (int(s) for s in args.scales.split(",")):
+        if scale <= 24:
+            g = _graph(seraph, synth, torch, scale, 256)
+            runs = ([("sssp", s) for s in (0, 12345, 99, 777, 4242, 31337)] +
+                    [("pagerank", 0), ("bfs", 0), ("bfs", 12345)])
+            x, k, p = collect(seraph, torch, g, 2 << 30, 64, runs)
+        else:
+            g = _graph(seraph, synth, torch, scale, 512)
+            x, k, p = collect(seraph, torch, g, 16 << 30, 16, [("sssp", 0), ("pagerank", 0)])
+        xs += x
+        ks += k
+        ps += p
+        g.free()
+    X, K, Pr = np.concatenate(xs), np.concatenate(ks), np.concatenate(ps)
+    model = seraph.SchedModel(seed=args.seed)
+    losses = model.train(X, K, Pr, epochs=args.epochs, batch=256, lr=2e-3, seed=args.seed + 1)
+    kp, pp = model.infer(X)
+    params = model.get_params()
+    params.astype("<f4").tofile(args.out)
+    summary = {"rows": int(len(K)), "scales": args.scales, "epochs": args.epochs,
+               "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+               "k_accuracy": float(np.mean(kp == K)),
+               "k_within_1": float(np.mean(np.abs(kp - K) <= 1)),
+               "priority_mae": float(np.mean(np.abs(pp - Pr))),
+               "k_histogram": np.bincount(K, minlength=17)[1:].tolist(),
+               "seconds": time.time() - t0}
+    with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
+        json.dump(summary, f, indent=1)
+    print(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main()
