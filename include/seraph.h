@@ -319,6 +319,64 @@ int  seraph_sched_infer(const seraph_sched_model* m, const float* x, uint64_t n,
 int  seraph_sched_targets(const seraph_trace* t, float share, int32_t* k_out, float* prio_out);
 void seraph_sched_free(seraph_sched_model* m);
 
+/*
+ * Batched queries (not in the paper; SURVEY's batching pattern): many BFS /
+ * SSSP queries over many graphs resident in device memory, run by one
+ * persistent kernel that is captured in a CUDA graph.  Each query advances
+ * in frontier rounds (push relaxation over the out-edge CSR, label
+ * correcting, so the results are the exact distances / levels); the tiles of
+ * every query's rounds share one task ring.  The tile mapping -- one thread,
+ * one warp, or the whole CTA (edge-balanced) per frontier vertex -- and the
+ * tile size are chosen per graph by an autotuner that times each candidate
+ * on the graph's own queries (cached in the graph for later calls).
+ */
+typedef struct seraph_bgraph seraph_bgraph;   /* device-resident out-edge CSR */
+
+enum seraph_mapping { SERAPH_MAP_AUTO = 0, SERAPH_MAP_THREAD = 1, SERAPH_MAP_WARP = 2,
+                      SERAPH_MAP_CTA = 3 };
+
+typedef struct seraph_query {
+    uint32_t graph;             /* index into the graphs array                */
+    int32_t  algo;              /* SERAPH_SSSP or SERAPH_BFS                  */
+    uint32_t source;
+    uint32_t reserved;
+    uint32_t* out;              /* n_graph distances / levels, in out_mem     */
+} seraph_query;
+
+typedef struct seraph_batch_params {
+    int32_t  mapping;           /* seraph_mapping; AUTO = autotune per graph  */
+    uint32_t tile;              /* frontier vertices per task (0 = 256)       */
+    uint32_t use_graph;         /* 1: capture the launch in a CUDA graph      */
+    uint32_t replays;           /* timed repetitions (>= 1)                   */
+    uint32_t timeout_ms;        /* bound on every wait, device and host       */
+    uint32_t reserved;
+    void*    stream;            /* cudaStream_t, NULL = own                   */
+} seraph_batch_params;
+
+typedef struct seraph_batch_stats {
+    double   time_ms;           /* one batched launch (mean over replays)     */
+    double   tune_ms;           /* autotuning time (0 when cached)            */
+    uint64_t edges;             /* out-edges relaxed by all queries           */
+    uint64_t tasks;             /* tiles processed                            */
+    uint32_t rounds_max;        /* most frontier rounds of any query          */
+    uint32_t graph_captured;    /* 1 if the launch ran from a CUDA graph      */
+    uint32_t mapping[16];       /* chosen mapping of graphs 0..15             */
+    uint32_t tile[16];          /* chosen tile of graphs 0..15                */
+} seraph_batch_stats;
+
+/* Resident out-edge CSR (self-loops dropped, duplicates keep the smallest
+ * weight, weights in the narrowest lossless width); arguments as for
+ * seraph_graph_from_edges. */
+int  seraph_bgraph_from_edges(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                              const uint32_t* w, int mem, void* stream, seraph_bgraph** out);
+void seraph_bgraph_free(seraph_bgraph* g);
+int  seraph_batch_params_default(seraph_batch_params* p);
+/* Run nq queries over ng graphs (one device).  Errors: SERAPH_EINVAL,
+ * SERAPH_ETIMEOUT (a bounded wait in the kernel ran out), SERAPH_ECUDA. */
+int  seraph_batch_run(seraph_bgraph* const* graphs, uint32_t ng, const seraph_query* queries,
+                      uint32_t nq, int out_mem, const seraph_batch_params* p,
+                      seraph_batch_stats* stats);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* seraph_last_error(void);
 

@@ -19,7 +19,7 @@ from . import _capi as C
 from ._capi import SeraphError, INF
 
 __all__ = ["Graph", "run", "default_params", "SeraphError", "INF", "version", "SchedModel",
-           "TraceBuffer"]
+           "TraceBuffer", "BGraph", "batch_run"]
 
 
 def version() -> str:
@@ -253,3 +253,71 @@ def run(graph: Graph, algo, out=None, stream=None, **kw):
     st = C.Stats()
     C.check(C.lib().seraph_run(graph._h, ctypes.byref(p), po, mo, ctypes.byref(st)))
     return out, st.as_dict()
+
+
+class BGraph:
+    """Device-resident out-edge CSR for batched queries."""
+
+    def __init__(self, n, src, dst, w=None, stream=None):
+        ps, ms, ks = _ptr_mem(src)
+        pd, md, kd = _ptr_mem(dst)
+        pw, mw, kw = _ptr_mem(w)
+        for arr in (ks, kd, kw):
+            if arr is not None and not _is_u32(arr):
+                raise TypeError("edge arrays must hold 32-bit unsigned integers")
+        h = ctypes.c_void_p()
+        C.check(C.lib().seraph_bgraph_from_edges(n, int(len(src)), ps, pd, pw, ms,
+                                                 _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        self.n = int(n)
+
+    def free(self):
+        if self._h and self._h.value:
+            C.lib().seraph_bgraph_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def batch_run(graphs, queries, outs=None, stream=None, **kw):
+    """Run queries [(graph index, "bfs"|"sssp", source), ...] in one batched
+    launch.  `outs` may give one preallocated array per query (numpy or torch,
+    all on the host or all on the device); by default numpy arrays are
+    returned.  Keyword arguments override seraph_batch_params (mapping may be
+    "auto", "thread", "warp" or "cta")."""
+    p = C.BatchParams()
+    C.check(C.lib().seraph_batch_params_default(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k == "mapping" and isinstance(v, str):
+            v = C.MAPPINGS[v]
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    p.stream = _stream_ptr(stream)
+    if outs is None:
+        # the library validates indices; an out-of-range one still needs a buffer
+        outs = [np.empty(graphs[g].n if 0 <= g < len(graphs) else 1, dtype=np.uint32)
+                for g, _, _ in queries]
+    arr = (C.Query * len(queries))()
+    keep = []
+    mem = None
+    for i, ((g, algo, src), o) in enumerate(zip(queries, outs)):
+        po, mo, ko = _ptr_mem(o)
+        keep.append(ko)
+        if mem is None:
+            mem = mo
+        elif mem != mo:
+            raise ValueError("all outputs must live in the same memory")
+        arr[i] = C.Query(g, C.ALGOS.get(algo, -1) if isinstance(algo, str) else algo, src, 0, po)
+    hs = (ctypes.c_void_p * len(graphs))(*[g._h.value for g in graphs])
+    st = C.BatchStats()
+    C.check(C.lib().seraph_batch_run(hs, len(graphs), arr, len(queries), mem, ctypes.byref(p),
+                                     ctypes.byref(st)))
+    stats = {k: getattr(st, k) for k, _ in st._fields_ if k not in ("mapping", "tile")}
+    stats["mapping"] = list(st.mapping)[:len(graphs)]
+    stats["tile"] = list(st.tile)[:len(graphs)]
+    return outs, stats

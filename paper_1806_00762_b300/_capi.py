@@ -80,6 +80,23 @@ class Trace(ctypes.Structure):
 
 
 SCHED_FEATURES, SCHED_OUTPUTS, SCHED_PARAMS = 16, 17, 6353
+MAP_AUTO, MAP_THREAD, MAP_WARP, MAP_CTA = 0, 1, 2, 3
+MAPPINGS = {"auto": MAP_AUTO, "thread": MAP_THREAD, "warp": MAP_WARP, "cta": MAP_CTA}
+
+
+class Query(ctypes.Structure):
+    _fields_ = [("graph", u32), ("algo", i32), ("source", u32), ("reserved", u32), ("out", vp)]
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("mapping", i32), ("tile", u32), ("use_graph", u32), ("replays", u32),
+                ("timeout_ms", u32), ("reserved", u32), ("stream", vp)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("time_ms", dbl), ("tune_ms", dbl), ("edges", u64), ("tasks", u64),
+                ("rounds_max", u32), ("graph_captured", u32), ("mapping", u32 * 16),
+                ("tile", u32 * 16)]
 
 # name -> (restype, argtypes); every symbol include/seraph.h declares
 PROTOTYPES = {
@@ -105,6 +122,12 @@ PROTOTYPES = {
     "seraph_sched_infer": (ctypes.c_int, [vp, vp, u64, ctypes.c_int, vp, vp]),
     "seraph_sched_targets": (ctypes.c_int, [ctypes.POINTER(Trace), ctypes.c_float, vp, vp]),
     "seraph_sched_free": (None, [vp]),
+    "seraph_bgraph_from_edges": (ctypes.c_int, [u64, u64, vp, vp, vp, ctypes.c_int, vp,
+                                                ctypes.POINTER(vp)]),
+    "seraph_bgraph_free": (None, [vp]),
+    "seraph_batch_params_default": (ctypes.c_int, [ctypes.POINTER(BatchParams)]),
+    "seraph_batch_run": (ctypes.c_int, [vp, u32, vp, u32, ctypes.c_int,
+                                        ctypes.POINTER(BatchParams), ctypes.POINTER(BatchStats)]),
     "seraph_last_error": (ctypes.c_char_p, []),
     "seraph_version": (ctypes.c_char_p, []),
 }

@@ -1,0 +1,566 @@
+// Batched multi-query BFS/SSSP over many resident graphs in one persistent
+// kernel (not in the paper: the north-star's batching pattern for many
+// sources and many small graphs).
+//
+// Each query keeps its own distances and two frontier lists and advances in
+// rounds; a round's frontier is cut into tiles of T vertices, and every tile
+// is one task.  Tasks of all queries share one ring of task slots.  A block
+// claims the next task index, waits until that slot is published, processes
+// the tile (push relaxation over the out-edge CSR: atomicMin on the
+// destination's distance, improved vertices go to the next frontier once per
+// round), then counts the tile done; the block that finishes a query's last
+// tile of a round publishes the query's next round.  No block ever waits for
+// a block that has not started, so the kernel needs no co-residency; every
+// wait has an iteration limit after which the kernel records an error and
+// returns.  Label-correcting relaxation reaches the exact distances / levels
+// whatever the interleaving.
+//
+// Mappings of a tile (picked per graph by the autotuner): one thread per
+// frontier vertex, one warp per frontier vertex, or the whole CTA over the
+// tile's edges (edge-balanced: a block scan of the tile's degrees, then one
+// thread per edge).
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "graph.hpp"
+
+
+namespace seraph {
+namespace {
+
+constexpr int kNT = 256;
+constexpr unsigned long long kConsumed = ~0ull;
+
+struct BGraphDev {
+    const uint64_t* off;
+    const uint32_t* col;
+    const uint8_t* w;
+    uint32_t n, wbytes;
+};
+
+struct BQuery {
+    uint32_t graph, algo, source, mapping, tile;
+    uint32_t round, cur_n, next_n, tiles_total, tiles_done, done, pad;
+    uint32_t* dist;
+    uint32_t* stamp;
+    uint32_t* front[2];
+};
+
+struct BGlobal {
+    unsigned long long head, tail, edges, tasks;
+    unsigned active, err, max_round, pad;
+};
+
+struct TaskSlot {
+    unsigned long long seq;  // task index + 1 once published, kConsumed once read, 0 initially
+    uint32_t q, tile;
+};
+
+__device__ __forceinline__ uint32_t weight_at(const BGraphDev& g, uint64_t e) {
+    if (!g.w) return 1u;
+    if (g.wbytes == 1) return g.w[e];
+    if (g.wbytes == 2) return ((const uint16_t*)g.w)[e];
+    return ((const uint32_t*)g.w)[e];
+}
+
+// Relax edge (u -> v) with candidate distance cand; push v on improvement.
+__device__ __forceinline__ bool relax(const BQuery& Q, uint32_t v, uint32_t cand) {
+    const uint32_t old = atomicMin(&Q.dist[v], cand);
+    if (cand >= old) return false;
+    return atomicMax(&Q.stamp[v], Q.round + 1) < Q.round + 1;  // first push this round
+}
+
+// Warp-aggregated append of `push` lanes' vertices to q's next frontier.
+__device__ __forceinline__ void push_next(BQuery* qs, uint32_t q, const BQuery& Q, bool push,
+                                          uint32_t v) {
+    const unsigned m = __ballot_sync(kFull, push);
+    if (!m) return;
+    const unsigned leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane_id() == leader) base = atomicAdd(&qs[q].next_n, __popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (push) Q.front[(Q.round + 1) & 1][base + __popc(m & lanemask_lt())] = v;
+}
+
+__device__ __forceinline__ uint32_t cand_of(const BQuery& Q, uint32_t du, uint32_t w, bool& ok) {
+    const uint32_t c = du + (Q.algo == SERAPH_SSSP ? w : 1u);
+    ok = c >= du && c != SERAPH_INF;  // overflowing candidates are dropped
+    return c;
+}
+
+// Query record as last published (read through L2: L1 is not coherent
+// across SMs and this kernel outlives many rounds).
+__device__ __forceinline__ BQuery load_query(const BQuery* p) {
+    BQuery Q;
+    const volatile BQuery* v = p;
+    Q.graph = v->graph; Q.algo = v->algo; Q.source = v->source; Q.mapping = v->mapping;
+    Q.tile = v->tile; Q.round = v->round; Q.cur_n = v->cur_n; Q.next_n = 0;
+    Q.tiles_total = 0; Q.tiles_done = 0; Q.done = 0; Q.pad = 0;
+    Q.dist = v->dist; Q.stamp = v->stamp; Q.front[0] = v->front[0]; Q.front[1] = v->front[1];
+    return Q;
+}
+
+// One task: tile `tile` of query q's current frontier.  Returns edges relaxed.
+// Frontier entries and distances are mutable across rounds: read via L2.
+__device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, uint32_t q,
+                                           uint32_t tile, uint64_t* s_pref, uint32_t* s_u) {
+    const BQuery Q = load_query(qs + q);
+    const BGraphDev G = graphs[Q.graph];
+    const uint32_t* cur = Q.front[Q.round & 1];
+    const uint32_t t0 = tile * Q.tile;
+    const uint32_t cnt = min(Q.tile, Q.cur_n - t0);
+    unsigned long long edges = 0;
+    if (Q.mapping == SERAPH_MAP_THREAD) {
+        for (uint32_t base = 0; base < cnt; base += kNT) {  // warps stay converged for the ballot
+            const uint32_t i = base + threadIdx.x;
+            uint32_t u = 0, du = 0;
+            uint64_t b = 0, e = 0;
+            if (i < cnt) {
+                u = __ldcg(cur + t0 + i);
+                du = __ldcg(Q.dist + u);
+                b = G.off[u];
+                e = G.off[u + 1];
+            }
+            edges += e - b;
+            for (uint64_t k = b;; ++k) {
+                const bool act = k < e;
+                if (!__any_sync(kFull, act)) break;
+                bool push = false;
+                uint32_t v = 0;
+                if (act) {
+                    v = G.col[k];
+                    bool ok;
+                    const uint32_t c = cand_of(Q, du, weight_at(G, k), ok);
+                    push = ok && relax(Q, v, c);
+                }
+                push_next(qs, q, Q, push, v);
+            }
+        }
+    } else if (Q.mapping == SERAPH_MAP_WARP) {
+        const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+        for (uint32_t i = warp; i < cnt; i += kNT / 32) {
+            const uint32_t u = __ldcg(cur + t0 + i);
+            const uint32_t du = __ldcg(Q.dist + u);
+            const uint64_t b = G.off[u], e = G.off[u + 1];
+            if (lane == 0) edges += e - b;
+            for (uint64_t k0 = b; k0 < e; k0 += 32) {
+                const uint64_t k = k0 + lane;
+                bool push = false;
+                uint32_t v = 0;
+                if (k < e) {
+                    v = G.col[k];
+                    bool ok;
+                    const uint32_t c = cand_of(Q, du, weight_at(G, k), ok);
+                    push = ok && relax(Q, v, c);
+                }
+                push_next(qs, q, Q, push, v);
+            }
+        }
+    } else {  // edge-balanced over the tile (tile <= kMaxCtaTile)
+        __shared__ uint64_t ws[kNT / 32 + 1];
+        for (uint32_t base = 0; base < cnt; base += kNT) {
+            const uint32_t i = base + threadIdx.x;
+            uint64_t d = 0;
+            if (i < cnt) {
+                const uint32_t u = __ldcg(cur + t0 + i);
+                s_u[i] = u;
+                d = G.off[u + 1] - G.off[u];
+            }
+            uint64_t tot;
+            const uint64_t ex = block_excl_scan<kNT>(d, ws, &tot);
+            const uint64_t run = base ? s_pref[base] : 0;
+            if (i < cnt) s_pref[i] = run + ex;
+            if (threadIdx.x == 0) s_pref[min(base + kNT, cnt)] = run + tot;
+            __syncthreads();
+        }
+        const uint64_t total = s_pref[cnt];
+        edges = threadIdx.x == 0 ? total : 0;
+        for (uint64_t k0 = 0; k0 < total; k0 += kNT) {
+            const uint64_t k = k0 + threadIdx.x;
+            bool push = false;
+            uint32_t v = 0;
+            if (k < total) {
+                uint32_t lo = 0, hi = cnt - 1;  // largest i with s_pref[i] <= k
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (s_pref[mid] <= k) lo = mid; else hi = mid - 1;
+                }
+                const uint32_t u = s_u[lo];
+                const uint64_t e = G.off[u] + (k - s_pref[lo]);
+                v = G.col[e];
+                bool ok;
+                const uint32_t c = cand_of(Q, __ldcg(Q.dist + u), weight_at(G, e), ok);
+                push = ok && relax(Q, v, c);
+            }
+            push_next(qs, q, Q, push, v);
+        }
+        __syncthreads();
+    }
+    return edges;
+}
+
+constexpr uint32_t kMaxCtaTile = 2048;
+
+// Publish tasks [t0, t0 + count) = (q, tile 0..count-1); the whole block helps.
+__device__ bool publish(TaskSlot* ring, unsigned long long mask, unsigned long long t0,
+                        uint32_t count, uint32_t q, unsigned long long spin_limit) {
+    bool ok = true;
+    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+        TaskSlot* sl = &ring[(t0 + i) & mask];
+        unsigned long long spins = 0;
+        for (;;) {  // the slot's previous task must have been read
+            const unsigned long long s = *(volatile unsigned long long*)&sl->seq;
+            if (s == 0 || s == kConsumed) break;
+            if (++spins > spin_limit) { ok = false; break; }
+            __nanosleep(32);
+        }
+        if (!ok) break;
+        sl->q = q;
+        sl->tile = i;
+        __threadfence();
+        *(volatile unsigned long long*)&sl->seq = t0 + i + 1;
+    }
+    return ok;
+}
+
+__global__ void __launch_bounds__(kNT) batch_kernel(const BGraphDev* graphs, BQuery* qs,
+                                                    BGlobal* gl, TaskSlot* ring,
+                                                    unsigned long long mask,
+                                                    unsigned long long spin_limit) {
+    __shared__ uint64_t s_pref[kMaxCtaTile + 1];
+    __shared__ uint32_t s_u[kMaxCtaTile];
+    __shared__ uint32_t s_q, s_tile, s_last, s_count;
+    __shared__ int s_exit;
+    __shared__ unsigned long long s_t0;
+    __shared__ unsigned long long s_edges;
+    if (threadIdx.x == 0) s_edges = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long t = atomicAdd(&gl->head, 1ull);
+            TaskSlot* sl = &ring[t & mask];
+            unsigned long long spins = 0;
+            s_exit = 0;
+            for (;;) {
+                const unsigned long long s = *(volatile unsigned long long*)&sl->seq;
+                if (s == t + 1) {
+                    __threadfence();
+                    s_q = sl->q;
+                    s_tile = sl->tile;
+                    *(volatile unsigned long long*)&sl->seq = kConsumed;
+                    break;
+                }
+                if (*(volatile unsigned*)&gl->active == 0) { s_exit = 1; break; }
+                if (*(volatile unsigned*)&gl->err) { s_exit = 1; break; }
+                if (++spins > spin_limit) { atomicOr(&gl->err, 1u); s_exit = 1; break; }
+                __nanosleep(64);
+            }
+        }
+        __syncthreads();
+        if (s_exit) break;
+        const uint32_t q = s_q;
+        const unsigned long long e = process_tile(graphs, qs, q, s_tile, s_pref, s_u);
+        atomicAdd(&s_edges, e);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();  // this tile's frontier pushes before its completion count
+            const uint32_t done = atomicAdd(&qs[q].tiles_done, 1u) + 1;
+            s_last = done == *(volatile uint32_t*)&qs[q].tiles_total;
+            if (s_last) {  // advance query q to its next round
+                __threadfence();
+                BQuery* Q = &qs[q];
+                const uint32_t nn = *(volatile uint32_t*)&Q->next_n;
+                Q->round = *(volatile uint32_t*)&Q->round + 1;
+                atomicMax(&gl->max_round, Q->round);
+                Q->cur_n = nn;
+                Q->next_n = 0;
+                Q->tiles_done = 0;
+                Q->tiles_total = (nn + *(volatile uint32_t*)&Q->tile - 1) / *(volatile uint32_t*)&Q->tile;
+                s_count = Q->tiles_total;
+                if (nn == 0) {
+                    Q->done = 1;
+                    __threadfence();
+                    atomicSub(&gl->active, 1u);
+                } else {
+                    __threadfence();
+                    s_t0 = atomicAdd(&gl->tail, (unsigned long long)s_count);
+                    atomicAdd(&gl->tasks, (unsigned long long)s_count);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_last && s_count && !publish(ring, mask, s_t0, s_count, q, spin_limit))
+            atomicOr(&gl->err, 2u);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&gl->edges, s_edges);
+}
+
+__global__ void init_dist_kernel(BQuery* qs, const BGraphDev* graphs, uint32_t nq) {
+    for (uint32_t q = blockIdx.y; q < nq; q += gridDim.y) {
+        const BQuery Q = qs[q];
+        const uint32_t n = graphs[Q.graph].n;
+        for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+            Q.dist[v] = v == Q.source ? 0u : SERAPH_INF;
+            Q.stamp[v] = 0;
+        }
+    }
+}
+
+// Round 0 of every query (frontier = its source) and the first nq tasks.
+__global__ void init_queries_kernel(BQuery* qs, uint32_t nq, BGlobal* gl, TaskSlot* ring,
+                                    unsigned long long cap) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        ring[i].seq = i < nq ? i + 1 : 0;
+        ring[i].q = (uint32_t)i;
+        ring[i].tile = 0;
+    }
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        BQuery& Q = qs[q];
+        Q.round = 0;
+        Q.cur_n = 1;
+        Q.next_n = 0;
+        Q.tiles_total = 1;
+        Q.tiles_done = 0;
+        Q.done = 0;
+        Q.front[0][0] = Q.source;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        gl->head = 0;
+        gl->tail = nq;
+        gl->edges = 0;
+        gl->tasks = nq;
+        gl->active = nq;
+        gl->err = 0;
+        gl->max_round = 0;
+    }
+}
+
+struct QSpec {
+    uint32_t graph, algo, source, mapping, tile;
+    uint32_t* out;  // device buffer for the distances, or null
+};
+
+struct Outcome {
+    float ms = 0.f;
+    unsigned long long edges = 0, tasks = 0;
+    unsigned max_round = 0;
+    bool captured = false;
+};
+
+void wait_stream(cudaStream_t s, uint32_t timeout_ms) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t r = cudaStreamQuery(s);
+        if (r == cudaSuccess) return;
+        if (r != cudaErrorNotReady) SR_CUDA(r);
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        SR_CHECK(ms < timeout_ms, SERAPH_ETIMEOUT, "timed out waiting for the batched kernel");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+// One batched launch over `qs` (distances stay in q.out when given, else in
+// scratch); `replays` timed repetitions, through a captured CUDA graph if
+// `use_graph`.  Distances of the last repetition are left in `dist_out[q]`.
+Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vector<QSpec>& qs,
+                     bool use_graph, uint32_t replays, uint32_t timeout_ms, cudaStream_t s,
+                     std::vector<uint32_t*>* dist_out, std::vector<DevBuf<uint32_t>>* hold) {
+    const uint32_t nq = (uint32_t)qs.size();
+    std::vector<BGraphDev> gd(graphs.size());
+    for (size_t i = 0; i < graphs.size(); ++i) {
+        const seraph_bgraph* g = graphs[i];
+        gd[i] = BGraphDev{g->adj.off.p, g->adj.col.p, g->weighted ? g->adj.wptr() : nullptr,
+                          (uint32_t)g->n, g->adj.wbytes};
+    }
+    std::vector<BQuery> qh(nq);
+    hold->clear();
+    hold->reserve(4 * (size_t)nq);
+    uint64_t tiles = 0;
+    uint32_t max_n = 1;
+    for (uint32_t q = 0; q < nq; ++q) {
+        const QSpec& Q = qs[q];
+        const uint64_t n = graphs[Q.graph]->n;
+        max_n = std::max<uint32_t>(max_n, (uint32_t)n);
+        BQuery b{};
+        b.graph = Q.graph; b.algo = Q.algo; b.source = Q.source; b.mapping = Q.mapping; b.tile = Q.tile;
+        if (Q.out) {
+            b.dist = Q.out;
+        } else {
+            hold->emplace_back(n);
+            b.dist = hold->back().p;
+        }
+        hold->emplace_back(n); b.stamp = hold->back().p;
+        hold->emplace_back(n); b.front[0] = hold->back().p;
+        hold->emplace_back(n); b.front[1] = hold->back().p;
+        qh[q] = b;
+        tiles += (n + Q.tile - 1) / Q.tile;
+        if (dist_out) (*dist_out)[q] = b.dist;
+    }
+    const int sms = device_sms();
+    const unsigned blocks = (unsigned)sms * 4;
+    unsigned long long cap = 1024;
+    while (cap < tiles + nq + 4ull * blocks + 1024) cap <<= 1;
+    DevBuf<BGraphDev> d_g(gd.size());
+    DevBuf<BQuery> d_q(nq);
+    DevBuf<BGlobal> d_gl(1);
+    DevBuf<TaskSlot> d_ring(cap);
+    SR_CUDA(cudaMemcpyAsync(d_g.p, gd.data(), gd.size() * sizeof(BGraphDev), cudaMemcpyHostToDevice, s));
+    SR_CUDA(cudaMemcpyAsync(d_q.p, qh.data(), nq * sizeof(BQuery), cudaMemcpyHostToDevice, s));
+    // ~15 polls per microsecond with the back-off: a limit of timeout_ms
+    const unsigned long long spin_limit = (unsigned long long)timeout_ms * 15000ull;
+    auto enqueue = [&](cudaStream_t st) {
+        const dim3 ig((max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64, std::min<uint32_t>(nq, 65535));
+        init_dist_kernel<<<ig, 256, 0, st>>>(d_q.p, d_g.p, nq);
+        init_queries_kernel<<<(unsigned)std::min<unsigned long long>((cap + 255) / 256, 4096), 256, 0, st>>>(
+            d_q.p, nq, d_gl.p, d_ring.p, cap);
+        batch_kernel<<<blocks, kNT, 0, st>>>(d_g.p, d_q.p, d_gl.p, d_ring.p, cap - 1, spin_limit);
+    };
+    Outcome out;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (use_graph) {
+        SR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        enqueue(s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (ce == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+            out.captured = true;
+        } else {
+            (void)cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+        }
+    }
+    cudaEvent_t e0, e1;
+    SR_CUDA(cudaEventCreate(&e0));
+    SR_CUDA(cudaEventCreate(&e1));
+    const uint32_t reps = std::max<uint32_t>(replays, 1);
+    SR_CUDA(cudaEventRecord(e0, s));
+    for (uint32_t r = 0; r < reps; ++r) {
+        if (out.captured) SR_CUDA(cudaGraphLaunch(exec, s));
+        else enqueue(s);
+        SR_LAUNCH();
+    }
+    SR_CUDA(cudaEventRecord(e1, s));
+    try {
+        wait_stream(s, timeout_ms * reps + 1000);
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    float ms = 0.f;
+    SR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    BGlobal gl;
+    SR_CUDA(cudaMemcpy(&gl, d_gl.p, sizeof(gl), cudaMemcpyDeviceToHost));
+    SR_CHECK(gl.err == 0, SERAPH_ETIMEOUT, "batched kernel: a bounded wait ran out (status " +
+                                               std::to_string(gl.err) + ")");
+    out.ms = ms / reps;
+    out.edges = gl.edges;
+    out.tasks = gl.tasks;
+    out.max_round = gl.max_round;
+    return out;
+}
+
+}  // namespace
+
+void bgraph_build(seraph_bgraph* g, uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                  const uint32_t* w, int mem, cudaStream_t s) {
+    SR_CHECK(n >= 1 && n <= 0xFFFFFFFEull, SERAPH_EINVAL, "n must be in [1, 2^32-2]");
+    SR_CHECK(mem == SERAPH_MEM_HOST || mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad mem kind");
+    SR_CHECK(m == 0 || (src && dst), SERAPH_EINVAL, "src/dst must not be NULL");
+    SR_CUDA(cudaGetDevice(&g->device));
+    g->n = n;
+    g->m_raw = m;
+    g->weighted = w != nullptr;
+    // rows = sources: the sorted adjacency of the swapped edge list
+    sorted_adjacency(n, m, dst, src, w, mem, false, s, g->adj);
+}
+
+int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* qin, uint32_t nq,
+              int out_mem, const seraph_batch_params* P, seraph_batch_stats* st) {
+    SR_CHECK(graphs_in && qin && P && ng >= 1 && nq >= 1, SERAPH_EINVAL, "bad batch arguments");
+    SR_CHECK(out_mem == SERAPH_MEM_HOST || out_mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad out_mem");
+    SR_CHECK(P->mapping >= SERAPH_MAP_AUTO && P->mapping <= SERAPH_MAP_CTA, SERAPH_EINVAL, "bad mapping");
+    SR_CHECK(P->tile == 0 || (P->tile <= (1u << 20)), SERAPH_EINVAL, "bad tile");
+    std::vector<seraph_bgraph*> graphs(graphs_in, graphs_in + ng);
+    for (auto* g : graphs) SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
+    SR_CUDA(cudaSetDevice(graphs[0]->device));
+    Stream s;
+    s.use(P->stream);
+    seraph_batch_stats S{};
+    auto t_tune = std::chrono::steady_clock::now();
+    // per-graph mapping and tile: fixed, cached, or autotuned on the graph's own queries
+    std::vector<uint32_t> gmap(ng), gtile(ng);
+    for (uint32_t gi = 0; gi < ng; ++gi) {
+        if (P->mapping != SERAPH_MAP_AUTO) {
+            gmap[gi] = (uint32_t)P->mapping;
+            gtile[gi] = P->tile ? P->tile : 256;
+            continue;
+        }
+        if (graphs[gi]->tuned_mapping) {
+            gmap[gi] = graphs[gi]->tuned_mapping;
+            gtile[gi] = graphs[gi]->tuned_tile;
+            continue;
+        }
+        std::vector<QSpec> sub;
+        std::vector<seraph_bgraph*> one{graphs[gi]};
+        for (uint32_t q = 0; q < nq; ++q)
+            if (qin[q].graph == gi) sub.push_back(QSpec{0, (uint32_t)qin[q].algo, qin[q].source, 0, 0, nullptr});
+        float best = 1e30f;
+        uint32_t bm = SERAPH_MAP_CTA, bt = 256;
+        if (!sub.empty()) {
+            for (uint32_t mp : {(uint32_t)SERAPH_MAP_THREAD, (uint32_t)SERAPH_MAP_WARP, (uint32_t)SERAPH_MAP_CTA})
+                for (uint32_t tl : {64u, 256u, 1024u}) {
+                    for (auto& x : sub) { x.mapping = mp; x.tile = tl; }
+                    std::vector<DevBuf<uint32_t>> hold;
+                    const Outcome o = launch_batch(one, sub, false, 2, P->timeout_ms, s.s, nullptr, &hold);
+                    if (o.ms < best) { best = o.ms; bm = mp; bt = tl; }
+                }
+        }
+        graphs[gi]->tuned_mapping = (int)bm;
+        graphs[gi]->tuned_tile = bt;
+        gmap[gi] = bm;
+        gtile[gi] = bt;
+    }
+    S.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_tune).count();
+
+    std::vector<QSpec> qs(nq);
+    for (uint32_t q = 0; q < nq; ++q) {
+        const seraph_query& Q = qin[q];
+        SR_CHECK(Q.graph < ng, SERAPH_EINVAL, "query graph index out of range");
+        SR_CHECK(Q.algo == SERAPH_SSSP || Q.algo == SERAPH_BFS, SERAPH_EINVAL, "batched queries are SSSP or BFS");
+        SR_CHECK(Q.source < graphs[Q.graph]->n, SERAPH_EINVAL, "query source >= n");
+        SR_CHECK(Q.out != nullptr, SERAPH_EINVAL, "query output must not be NULL");
+        const uint32_t algo = (Q.algo == SERAPH_SSSP && !graphs[Q.graph]->weighted) ? SERAPH_BFS : Q.algo;
+        uint32_t tile = gtile[Q.graph];
+        if (gmap[Q.graph] == SERAPH_MAP_CTA) tile = std::min<uint32_t>(tile, kMaxCtaTile);
+        qs[q] = QSpec{Q.graph, algo, Q.source, gmap[Q.graph], tile,
+                      out_mem == SERAPH_MEM_DEVICE ? Q.out : nullptr};
+    }
+    std::vector<uint32_t*> dist(nq);
+    std::vector<DevBuf<uint32_t>> hold;
+    const Outcome o = launch_batch(graphs, qs, P->use_graph != 0, P->replays, P->timeout_ms, s.s, &dist, &hold);
+    if (out_mem == SERAPH_MEM_HOST)
+        for (uint32_t q = 0; q < nq; ++q)
+            SR_CUDA(cudaMemcpy(qin[q].out, dist[q], graphs[qin[q].graph]->n * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost));
+    SR_CUDA(cudaStreamSynchronize(s.s));
+    S.time_ms = o.ms;
+    S.edges = o.edges;
+    S.tasks = o.tasks;
+    S.rounds_max = o.max_round;
+    S.graph_captured = o.captured;
+    for (uint32_t gi = 0; gi < ng && gi < 16; ++gi) { S.mapping[gi] = gmap[gi]; S.tile[gi] = gtile[gi]; }
+    if (st) *st = S;
+    return SERAPH_OK;
+}
+
+}  // namespace seraph

@@ -13,7 +13,12 @@
 
 namespace seraph {
 int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, seraph_stats* st);
+void bgraph_build(seraph_bgraph* g, uint64_t n, uint64_t m, const uint32_t* src,
+                  const uint32_t* dst, const uint32_t* w, int mem, cudaStream_t s);
+int batch_run(seraph_bgraph* const* graphs, uint32_t ng, const seraph_query* q, uint32_t nq,
+              int out_mem, const seraph_batch_params* P, seraph_batch_stats* st);
 }
+
 
 namespace {
 
@@ -327,6 +332,56 @@ void seraph_sched_free(seraph_sched_model* m) {
     if (!m) return;
     cudaSetDevice(m->device);
     delete m;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- batched queries
+
+extern "C" {
+
+int seraph_bgraph_from_edges(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                             const uint32_t* w, int mem, void* stream, seraph_bgraph** out) {
+    return guarded([&] {
+        SR_CHECK(out != nullptr, SERAPH_EINVAL, "out must not be NULL");
+        *out = nullptr;
+        seraph::Stream s;
+        s.use(stream);
+        auto* g = new seraph_bgraph();
+        try {
+            seraph::bgraph_build(g, n, m, src, dst, w, mem, s.s);
+        } catch (...) {
+            delete g;
+            throw;
+        }
+        *out = g;
+        return SERAPH_OK;
+    });
+}
+
+void seraph_bgraph_free(seraph_bgraph* g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    delete g;
+}
+
+int seraph_batch_params_default(seraph_batch_params* p) {
+    return guarded([&] {
+        SR_CHECK(p != nullptr, SERAPH_EINVAL, "null params");
+        std::memset(p, 0, sizeof(*p));
+        p->mapping = SERAPH_MAP_AUTO;
+        p->tile = 0;
+        p->use_graph = 1;
+        p->replays = 1;
+        p->timeout_ms = 60000;
+        return SERAPH_OK;
+    });
+}
+
+int seraph_batch_run(seraph_bgraph* const* graphs, uint32_t ng, const seraph_query* queries,
+                     uint32_t nq, int out_mem, const seraph_batch_params* p,
+                     seraph_batch_stats* stats) {
+    return guarded([&] { return seraph::batch_run(graphs, ng, queries, nq, out_mem, p, stats); });
 }
 
 }  // extern "C"

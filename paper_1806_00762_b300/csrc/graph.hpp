@@ -41,6 +41,21 @@ struct seraph_graph {
 };
 
 namespace seraph {
+struct Adjacency;
+}
+
+namespace seraph {
+struct Adjacency {
+    uint64_t E = 0;
+    uint32_t wbytes = 4;
+    DevBuf<uint64_t> off;   // n+1 row offsets
+    DevBuf<uint32_t> col;   // other endpoint, ascending within a row
+    DevBuf<uint32_t> wcol;  // weights if stored 4 bytes wide
+    DevBuf<uint8_t> wnar;   // weights if narrowed to 1 or 2 bytes
+    const uint8_t* wptr() const { return wbytes < 4 ? wnar.p : (const uint8_t*)wcol.p; }
+};
+void sorted_adjacency(uint64_t n, uint64_t m, const uint32_t* lo, const uint32_t* hi,
+                      const uint32_t* w, int mem, bool sym, cudaStream_t s, Adjacency& A);
 void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src,
                  const uint32_t* dst, const uint32_t* w, int mem, uint32_t flags,
                  uint32_t num_pages, cudaStream_t s);
@@ -50,3 +65,13 @@ void build_graph_csr(seraph_graph* g, uint64_t n, const uint64_t* row_off, const
 void export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* row, uint32_t* w,
                 uint32_t* out_degree);
 }  // namespace seraph
+
+// Device-resident out-edge CSR for batched queries (batch.cu).
+struct seraph_bgraph {
+    int device = 0;
+    uint64_t n = 0, m_raw = 0;
+    bool weighted = false;
+    seraph::Adjacency adj;        // rows = sources
+    int tuned_mapping = 0;        // 0: not tuned yet
+    uint32_t tuned_tile = 0;
+};

@@ -446,32 +446,23 @@ const T* to_device(const T* p, uint64_t count, int mem, DevBuf<T>& hold, cudaStr
 
 }  // namespace
 
-void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in,
-                 const uint32_t* dst_in, const uint32_t* w_in, int mem, uint32_t flags,
-                 uint32_t P, cudaStream_t s) {
-    SR_CHECK(n >= 1 && n <= 0xFFFFFFFEull, SERAPH_EINVAL, "n must be in [1, 2^32-2]");
-    SR_CHECK(P >= 1 && P <= (1u << 20), SERAPH_EINVAL, "num_pages must be in [1, 2^20]");
-    SR_CHECK(mem == SERAPH_MEM_HOST || mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad mem kind");
-    SR_CHECK(m == 0 || (src_in && dst_in), SERAPH_EINVAL, "src/dst must not be NULL");
-    SR_CHECK(m < (1ull << 36), SERAPH_EINVAL, "too many edges");
-    const bool sym = flags & SERAPH_SYMMETRIZE;
+// Sorted, deduplicated adjacency of raw edges (lo -> hi): rows are the `hi`
+// endpoints, each row lists its `lo` endpoints ascending.  With lo = source
+// and hi = destination this is the CSC of Sec. 3.1; with the two swapped it is
+// the out-edge CSR.  Self-loops are dropped, duplicates keep the smallest
+// weight, weights are narrowed to the smallest lossless width.
+void sorted_adjacency(uint64_t n, uint64_t m, const uint32_t* lo_in, const uint32_t* hi_in,
+                      const uint32_t* w_in, int mem, bool sym, cudaStream_t s, Adjacency& A) {
+    const uint64_t M = sym ? 2 * m : m;
     const bool weighted = w_in != nullptr;
-    SR_CUDA(cudaGetDevice(&g->device));
-    g->n = n;
-    g->m_raw = sym ? 2 * m : m;
-    g->num_pages = P;
-    g->weighted = weighted;
-    g->symmetrized = sym;
-
-    const uint64_t M = g->m_raw;
     const int b = bits_for(n);
     DevBuf<uint64_t> keys(M), keys_alt(M);
     DevBuf<uint32_t> vals, vals_alt;
     if (weighted) { vals.alloc(M); vals_alt.alloc(M); }
     {
         DevBuf<uint32_t> hs, hd, hw;
-        const uint32_t* src = to_device(src_in, m, mem, hs, s);
-        const uint32_t* dst = to_device(dst_in, m, mem, hd, s);
+        const uint32_t* src = to_device(lo_in, m, mem, hs, s);
+        const uint32_t* dst = to_device(hi_in, m, mem, hd, s);
         const uint32_t* w = to_device(w_in, m, mem, hw, s);
         if (m) {
             DevBuf<unsigned> bad(1);
@@ -495,7 +486,9 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     // dedupe + compaction
     uint64_t ntiles = (M + kTile - 1) / kTile;
     uint64_t E = 0;
-    DevBuf<uint32_t> col, dcol, wcol;
+    DevBuf<uint32_t> dcol;
+    DevBuf<uint32_t>& col = A.col;
+    DevBuf<uint32_t>& wcol = A.wcol;
     if (M) {
         DevBuf<uint32_t> cnt(ntiles);
         DevBuf<uint64_t> toff(ntiles + 1);
@@ -518,10 +511,10 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     }
     keys.release();
     vals.release();
-    g->m = E;
+    A.E = E;
     // Narrowest lossless weight width (Sec. 3.1: the page format keeps the
     // transferred data as compact as possible).
-    DevBuf<uint8_t> wnar;
+    DevBuf<uint8_t>& wnar = A.wnar;
     if (weighted && E) {
         DevBuf<unsigned> mx(1);
         SR_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned), s));
@@ -530,21 +523,47 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
         unsigned hmx = 0;
         SR_CUDA(cudaMemcpyAsync(&hmx, mx.p, 4, cudaMemcpyDeviceToHost, s));
         SR_CUDA(cudaStreamSynchronize(s));
-        g->wbytes = hmx <= 0xFFu ? 1 : (hmx <= 0xFFFFu ? 2 : 4);
-        if (g->wbytes < 4) {
-            wnar.alloc(E * g->wbytes);
-            narrow_kernel<<<grid_for(E), kNT, 0, s>>>(wcol.p, E, (int)g->wbytes, wnar.p);
+        A.wbytes = hmx <= 0xFFu ? 1 : (hmx <= 0xFFFFu ? 2 : 4);
+        if (A.wbytes < 4) {
+            wnar.alloc(E * A.wbytes);
+            narrow_kernel<<<grid_for(E), kNT, 0, s>>>(wcol.p, E, (int)A.wbytes, wnar.p);
             SR_LAUNCH();
             SR_CUDA(cudaStreamSynchronize(s));
             wcol.release();
         }
     }
-    const uint8_t* wsrc = g->wbytes < 4 ? wnar.p : (const uint8_t*)wcol.p;
-
-    DevBuf<uint64_t> col_off(n + 1);
-    col_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(dcol.p, E, n, col_off.p);
+    A.off.alloc(n + 1);
+    col_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(dcol.p, E, n, A.off.p);
     SR_LAUNCH();
     dcol.release();
+    SR_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in,
+                 const uint32_t* dst_in, const uint32_t* w_in, int mem, uint32_t flags,
+                 uint32_t P, cudaStream_t s) {
+    SR_CHECK(n >= 1 && n <= 0xFFFFFFFEull, SERAPH_EINVAL, "n must be in [1, 2^32-2]");
+    SR_CHECK(P >= 1 && P <= (1u << 20), SERAPH_EINVAL, "num_pages must be in [1, 2^20]");
+    SR_CHECK(mem == SERAPH_MEM_HOST || mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad mem kind");
+    SR_CHECK(m == 0 || (src_in && dst_in), SERAPH_EINVAL, "src/dst must not be NULL");
+    SR_CHECK(m < (1ull << 36), SERAPH_EINVAL, "too many edges");
+    const bool sym = flags & SERAPH_SYMMETRIZE;
+    const bool weighted = w_in != nullptr;
+    SR_CUDA(cudaGetDevice(&g->device));
+    g->n = n;
+    g->m_raw = sym ? 2 * m : m;
+    g->num_pages = P;
+    g->weighted = weighted;
+    g->symmetrized = sym;
+
+    Adjacency A;
+    sorted_adjacency(n, m, src_in, dst_in, w_in, mem, sym, s, A);
+    const uint64_t E = A.E;
+    g->m = E;
+    g->wbytes = A.wbytes;
+    DevBuf<uint32_t>& col = A.col;
+    const uint8_t* wsrc = A.wptr();
+    DevBuf<uint64_t>& col_off = A.off;
     g->d_zero_in.alloc((n + 31) / 32);
     zero_in_kernel<<<grid_for((n + 31) / 32), kNT, 0, s>>>(col_off.p, n, g->d_zero_in.p);
     SR_LAUNCH();

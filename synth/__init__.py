@@ -169,3 +169,24 @@ def has_out_edge(n: int, src: np.ndarray, dst: np.ndarray) -> np.ndarray:
     keep = src != dst
     mask[src[keep]] = True
     return mask
+
+
+# Batched-query workload: 16 R-MAT graphs of uneven size (scales 14..22,
+# edge factors 8..32, four quadrant skews), 256 queries split evenly between
+# BFS and SSSP, sources uniform over vertices that have an out-edge.
+BATCH_SKEWS = ((0.57, 0.19, 0.19, 0.05), (0.45, 0.15, 0.15, 0.25),
+               (0.25, 0.25, 0.25, 0.25), (0.70, 0.10, 0.10, 0.10))
+
+
+def batch_workload(n_graphs: int = 16, n_queries: int = 256, min_scale: int = 14,
+                   max_scale: int = 22, seed: int = 7):
+    """Graph specs (scale, edge_factor, abcd, seed) and query specs
+    (graph, algo, source-draw seed).  Scales are spread evenly from min to max."""
+    graphs = []
+    for i in range(n_graphs):
+        scale = min_scale + round(i * (max_scale - min_scale) / max(1, n_graphs - 1))
+        graphs.append(dict(scale=scale, edge_factor=(8, 16, 32)[i % 3],
+                           abcd=BATCH_SKEWS[i % 4], seed=seed * 1000 + i))
+    queries = [dict(graph=q % n_graphs, algo="bfs" if (q // n_graphs) % 2 == 0 else "sssp")
+               for q in range(n_queries)]
+    return graphs, queries

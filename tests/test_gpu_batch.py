@@ -1,0 +1,85 @@
+"""Batched multi-query BFS/SSSP (one persistent kernel over many resident
+graphs): every query bit-exact against the oracle, for every tile mapping,
+tile size, with and without CUDA-graph capture, host and device outputs."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1806_00762_b300 as seraph
+from paper_1806_00762_b300 import SeraphError
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def work():
+    specs, qspecs = synth.batch_workload(n_graphs=6, n_queries=48, min_scale=9, max_scale=13)
+    graphs, ogs, queries, refs = [], [], [], []
+    for i, sp in enumerate(specs):
+        n = 1 << sp["scale"]
+        src, dst = synth.rmat_edges(sp["scale"], sp["edge_factor"], sp["abcd"], sp["seed"])
+        w = synth.weights(src, dst)
+        graphs.append(seraph.BGraph(n, src, dst, w))
+        ogs.append(oracle.build_csr(n, src, dst, w))
+        srcs = iter(synth.pick_sources(n, synth.has_out_edge(n, src, dst), 64, seed=100 + i))
+        for q in qspecs:
+            if q["graph"] == i:
+                s = next(srcs)
+                queries.append((i, q["algo"], s))
+    for g, algo, s in queries:
+        refs.append(oracle.bfs(ogs[g], s) if algo == "bfs" else oracle.sssp(ogs[g], s))
+    return graphs, queries, refs
+
+
+CASES = [dict(mapping="thread", tile=64), dict(mapping="warp", tile=64),
+         dict(mapping="cta", tile=256), dict(mapping="thread", tile=1),
+         dict(mapping="cta", tile=2048), dict(mapping="warp", tile=1024, use_graph=0),
+         dict(mapping="auto")]
+
+
+@pytest.mark.parametrize("kw", CASES, ids=lambda k: "-".join(f"{a}{b}" for a, b in k.items()))
+def test_batch_matches_oracle(work, kw):
+    graphs, queries, refs = work
+    outs, st = seraph.batch_run(graphs, queries, **kw)
+    for o, r in zip(outs, refs):
+        assert np.array_equal(o, r)
+    assert st["edges"] > 0 and st["rounds_max"] >= 1
+    if kw.get("use_graph", 1):
+        assert st["graph_captured"] == 1
+
+
+def test_autotune_result_is_cached_and_device_outputs(work):
+    import torch
+    graphs, queries, refs = work
+    _, st1 = seraph.batch_run(graphs, queries, mapping="auto")
+    outs = [torch.empty(graphs[g].n, dtype=torch.int32, device="cuda") for g, _, _ in queries]
+    _, st2 = seraph.batch_run(graphs, queries, outs=outs, mapping="auto", replays=3)
+    assert st2["tune_ms"] < st1["tune_ms"] + 1.0 and st2["mapping"] == st1["mapping"]
+    for o, r in zip(outs, refs):
+        assert np.array_equal(o.cpu().numpy().view(np.uint32), r)
+
+
+def test_batch_edge_cases():
+    e = np.zeros(0, np.uint32)
+    g0 = seraph.BGraph(5, e, e, e)                       # no edges
+    src = np.array([0, 1, 2, 2], np.uint32)
+    dst = np.array([1, 2, 3, 3], np.uint32)
+    w = np.array([7, 255, 1, 9], np.uint32)
+    g1 = seraph.BGraph(6, src, dst, w)                   # vertex 5 isolated, a duplicate edge
+    outs, _ = seraph.batch_run([g0, g1], [(0, "bfs", 3), (1, "sssp", 0), (1, "bfs", 5), (1, "sssp", 4)])
+    INF = seraph.INF
+    assert list(outs[0]) == [INF, INF, INF, 0, INF]
+    assert list(outs[1]) == [0, 7, 262, 263, INF, INF]
+    assert list(outs[2]) == [INF] * 5 + [0]
+    assert list(outs[3]) == [INF, INF, INF, INF, 0, INF]
+
+
+def test_batch_invalid_arguments(work):
+    graphs, _, _ = work
+    with pytest.raises(SeraphError, match="EINVAL"):
+        seraph.batch_run(graphs, [(0, "bfs", graphs[0].n)])
+    with pytest.raises(SeraphError, match="EINVAL"):
+        seraph.batch_run(graphs, [(0, "cc", 0)])
+    with pytest.raises(SeraphError, match="EINVAL"):
+        seraph.batch_run(graphs, [(len(graphs), "bfs", 0)])
