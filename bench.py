@@ -52,6 +52,9 @@ def parse():
                     help="SSSP schedule: comma-separated seraph_params overrides")
     ap.add_argument("--pagerank", default="order=zigzag,window=1,slots=16,pvu=weak",
                     help="PageRank schedule: comma-separated seraph_params overrides")
+    ap.add_argument("--vertex-order", default="degree", choices=["degree", "natural"],
+                    help="degree: vertices numbered by non-increasing out-degree before the "
+                         "page cut (SERAPH_REORDER); natural: the generator's ids")
     ap.add_argument("--no-paper-schedule", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-scheduler comparison run")
@@ -132,7 +135,7 @@ def link_gbps(torch, nbytes=1 << 30, reps=5, chunks=4) -> float:
     return chunks * nbytes / (best / 1e3) / 1e9
 
 
-def build_graph(seraph, synth, torch, scale, pages):
+def build_graph(seraph, synth, torch, scale, pages, reorder=True):
     n = 1 << scale
     m = synth.rmat_config(scale).m
     src = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -140,7 +143,7 @@ def build_graph(seraph, synth, torch, scale, pages):
     w = torch.empty_like(src)
     synth.rmat_edges_device(scale, src.data_ptr(), dst.data_ptr(), w.data_ptr())
     torch.cuda.synchronize()
-    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=pages)
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=pages, reorder=reorder)
     del src, dst, w
     torch.cuda.empty_cache()
     return g
@@ -290,6 +293,7 @@ def main():
     sched = {"sssp": parse_sched(args.sssp), "pagerank": parse_sched(args.pagerank)}
     config = {"workload": f"rmat{args.scale}-ef16-streamed", "scale": args.scale, "edge_factor": 16,
               "pages": args.pages, "budget_gb": args.budget_gb, "algorithms": ["sssp", "pagerank"],
+              "vertex_order": args.vertex_order,
               "schedule": {"kind": "fixed", **sched},
               "inputs": "pinned host pages streamed each sweep (the method)",
               "l2_flush": "inputs larger than L2 (graph >= 2 GB per sweep)",
@@ -325,7 +329,8 @@ def main():
     import paper_1806_00762_b300 as seraph
 
     t_setup = time.time()
-    g = build_graph(seraph, synth, torch, args.scale, args.pages)
+    g = build_graph(seraph, synth, torch, args.scale, args.pages,
+                    reorder=args.vertex_order == "degree")
     info = g.info()
     E = info["m"]
     n = info["n"]

@@ -66,6 +66,15 @@ enum seraph_order { SERAPH_ORDER_CYCLIC = 0, SERAPH_ORDER_ZIGZAG = 1 };
 /* Graph flags. */
 #define SERAPH_SYMMETRIZE 1u  /* add (v,u) for every (u,v): the undirected view
                                  that weakly connected components run on      */
+#define SERAPH_REORDER    2u  /* number vertices internally in order of
+                                 non-increasing out-degree (ties: ascending
+                                 id) before the page cut.  A layout choice,
+                                 not in the paper: the gathered source values
+                                 of the most-read vertices become one compact
+                                 range that stays in L2.  Results, sources and
+                                 labels stay in the caller's ids; only the
+                                 page contents (export_csc, page_bounds) are
+                                 in internal ids (see seraph_graph_export_perm) */
 
 typedef struct seraph_graph seraph_graph;  /* opaque, library-owned */
 
@@ -84,7 +93,7 @@ typedef struct seraph_graph_info {
     uint32_t max_in_degree;
     uint32_t weight_width;      /* bytes per stored weight: 1, 2 or 4 (the
                                    narrowest that holds the largest weight) */
-    uint32_t reserved;
+    uint32_t reordered;         /* 1 if built with SERAPH_REORDER            */
 } seraph_graph_info;
 
 /*
@@ -124,6 +133,13 @@ int  seraph_graph_page_bounds(const seraph_graph* g, uint64_t* vb);
  * destination), w[m] weights (may be NULL), out_degree[n] (may be NULL). */
 int  seraph_graph_export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* row,
                              uint32_t* w, uint32_t* out_degree);
+
+/* The internal vertex order: perm[i] = the caller's id of internal vertex i
+ * (host array of n uint32).  The identity unless built with SERAPH_REORDER.
+ * With it, i < j implies outdeg(perm[i]) > outdeg(perm[j]), or equal
+ * out-degrees and perm[i] < perm[j]; out-degrees count kept edges (after
+ * SYMMETRIZE, self-loop removal and deduplication). */
+int  seraph_graph_export_perm(const seraph_graph* g, uint32_t* perm);
 
 void seraph_graph_free(seraph_graph* g);
 

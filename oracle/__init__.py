@@ -8,7 +8,9 @@ links or executes anything here, and this package never touches the product.
 The C part (``oracle.c``) writes out the plain definitions: Dijkstra, FIFO
 BFS, union-find weakly-connected components and FP64 PageRank power iteration
 (evaluation section "Graph Algorithms"; Sec. 4.3 for PageRank), the CSR/CSC
-build and the destination-range page cut (Sec. 3.1 "Subgraph Organization").
+build and the destination-range page cut (Sec. 3.1 "Subgraph Organization"),
+and the out-degree vertex order (``degree_order``; a layout outside the
+paper that renames vertices only).
 ``mlp.py`` holds the FP64 reference of the learned scheduler's network.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
@@ -128,6 +130,26 @@ def csc(g: CSR):
     wc = None if g.w is None else np.empty(max(g.m, 1), dtype=np.uint32)
     _L().oracle_csc(g.n, g.row_off, g.col, _ptr(g.w), col_off, row, _ptr(wc))
     return col_off, row[:g.m].copy(), (None if wc is None else wc[:g.m].copy())
+
+
+def degree_order(g: CSR) -> np.ndarray:
+    """perm[i] = the vertex listed i-th when vertices are ordered by
+    non-increasing out-degree (kept edges), ties by ascending id.
+
+    Not in the paper: the product may renumber vertices this way before the
+    page cut (a memory-layout choice that leaves every result unchanged).  The
+    plain definition is a stable two-key sort."""
+    deg = g.out_degree().astype(np.int64)
+    return np.lexsort((np.arange(g.n, dtype=np.int64), -deg)).astype(np.uint32)
+
+
+def relabel(g: CSR, perm) -> CSR:
+    """The same graph with vertex perm[i] renamed i (weights kept)."""
+    perm = _u32(perm)
+    inv = np.empty(g.n, dtype=np.uint32)
+    inv[perm] = np.arange(g.n, dtype=np.uint32)
+    src = np.repeat(np.arange(g.n, dtype=np.uint32), np.diff(g.row_off).astype(np.int64))
+    return build_csr(g.n, inv[src], inv[g.col], g.w)
 
 
 def page_cut(n: int, col_off: np.ndarray, P: int) -> np.ndarray:

@@ -52,6 +52,10 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+def _flags(symmetrize: bool, reorder: bool) -> int:
+    return (C.SYMMETRIZE if symmetrize else 0) | (C.REORDER if reorder else 0)
+
+
 class Graph:
     """Paged CSC graph in library-owned pinned host memory (Sec. 3.1)."""
 
@@ -59,7 +63,8 @@ class Graph:
         self._h = ctypes.c_void_p(handle)
 
     @classmethod
-    def from_edges(cls, n, src, dst, w=None, symmetrize=False, num_pages=1, stream=None):
+    def from_edges(cls, n, src, dst, w=None, symmetrize=False, num_pages=1, stream=None,
+                   reorder=False):
         ps, ms, ks = _ptr_mem(src)
         pd, md, kd = _ptr_mem(dst)
         pw, mw, kw = _ptr_mem(w)
@@ -72,20 +77,19 @@ class Graph:
             if arr is not None and not _is_u32(arr):
                 raise TypeError("edge arrays must hold 32-bit unsigned integers")
         out = ctypes.c_void_p()
-        C.check(C.lib().seraph_graph_from_edges(n, m, ps, pd, pw, ms,
-                                                C.SYMMETRIZE if symmetrize else 0, num_pages,
-                                                _stream_ptr(stream), ctypes.byref(out)))
+        C.check(C.lib().seraph_graph_from_edges(n, m, ps, pd, pw, ms, _flags(symmetrize, reorder),
+                                                num_pages, _stream_ptr(stream), ctypes.byref(out)))
         return cls(out.value)
 
     @classmethod
-    def from_csr(cls, n, row_off, col, w=None, symmetrize=False, num_pages=1, stream=None):
+    def from_csr(cls, n, row_off, col, w=None, symmetrize=False, num_pages=1, stream=None,
+                 reorder=False):
         pr, mr, kr = _ptr_mem(row_off)
         pc, mc, kc = _ptr_mem(col)
         pw, mw, kw = _ptr_mem(w)
         out = ctypes.c_void_p()
-        C.check(C.lib().seraph_graph_from_csr(n, pr, pc, pw, mr,
-                                              C.SYMMETRIZE if symmetrize else 0, num_pages,
-                                              _stream_ptr(stream), ctypes.byref(out)))
+        C.check(C.lib().seraph_graph_from_csr(n, pr, pc, pw, mr, _flags(symmetrize, reorder),
+                                              num_pages, _stream_ptr(stream), ctypes.byref(out)))
         return cls(out.value)
 
     def info(self) -> dict:
@@ -109,6 +113,12 @@ class Graph:
                                                 None if w is None else w.ctypes.data,
                                                 od.ctypes.data))
         return col_off, row[:i["m"]], (None if w is None else w[:i["m"]]), od
+
+    def perm(self) -> np.ndarray:
+        """Internal vertex order: perm[i] = the caller's id of internal vertex i."""
+        p = np.empty(self.info()["n"], dtype=np.uint32)
+        C.check(C.lib().seraph_graph_export_perm(self._h, p.ctypes.data))
+        return p
 
     def free(self):
         if self._h and self._h.value:

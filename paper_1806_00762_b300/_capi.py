@@ -35,6 +35,7 @@ SCHED_FIXED, SCHED_LEARNED = 0, 1
 ORDER_CYCLIC, ORDER_ZIGZAG = 0, 1
 ORDERS = {"cyclic": ORDER_CYCLIC, "zigzag": ORDER_ZIGZAG}
 SYMMETRIZE = 1
+REORDER = 2
 NOALLOC_MAX_VERTICES = 1 << 20
 INF = 0xFFFFFFFF
 
@@ -47,7 +48,7 @@ class GraphInfo(ctypes.Structure):
                 ("weight_bytes", u64), ("max_page_struct_bytes", u64),
                 ("max_page_weight_bytes", u64), ("num_pages", u32), ("weighted", u32),
                 ("symmetrized", u32), ("max_in_degree", u32), ("weight_width", u32),
-                ("reserved", u32)]
+                ("reordered", u32)]
 
 
 class Params(ctypes.Structure):
@@ -107,6 +108,7 @@ PROTOTYPES = {
     "seraph_graph_get_info": (ctypes.c_int, [vp, ctypes.POINTER(GraphInfo)]),
     "seraph_graph_page_bounds": (ctypes.c_int, [vp, vp]),
     "seraph_graph_export_csc": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+    "seraph_graph_export_perm": (ctypes.c_int, [vp, vp]),
     "seraph_graph_free": (None, [vp]),
     "seraph_params_default": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int]),
     "seraph_run": (ctypes.c_int, [vp, ctypes.POINTER(Params), vp, ctypes.c_int,

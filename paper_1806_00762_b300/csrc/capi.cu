@@ -114,6 +114,7 @@ int seraph_graph_get_info(const seraph_graph* g, seraph_graph_info* info) {
         info->symmetrized = g->symmetrized;
         info->max_in_degree = g->max_in_degree;
         info->weight_width = g->weighted ? g->wbytes : 0;
+        info->reordered = g->reordered;
         return SERAPH_OK;
     });
 }
@@ -132,6 +133,19 @@ int seraph_graph_export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* 
         SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
         SR_CHECK(w == nullptr || g->weighted, SERAPH_EINVAL, "graph has no weights");
         seraph::export_csc(g, col_off, row, w, out_degree);
+        return SERAPH_OK;
+    });
+}
+
+int seraph_graph_export_perm(const seraph_graph* g, uint32_t* perm) {
+    return guarded([&] {
+        SR_CHECK(g && perm, SERAPH_EINVAL, "null argument");
+        if (g->reordered) {
+            SR_CUDA(cudaSetDevice(g->device));
+            SR_CUDA(cudaMemcpy(perm, g->d_perm.p, g->n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        } else {
+            for (uint64_t i = 0; i < g->n; ++i) perm[i] = (uint32_t)i;
+        }
         return SERAPH_OK;
     });
 }

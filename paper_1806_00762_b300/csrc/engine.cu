@@ -526,11 +526,15 @@ __global__ void set_locs_kernel(PageLoc* loc, const uint32_t* vb, uint32_t first
     }
 }
 
+// CC labels start at the caller's vertex id (label0 = internal -> caller id
+// map of a reordered graph, or null for the identity), so the fixpoint label
+// is the smallest caller id in the component whatever the internal order.
 __global__ void init_min_kernel(uint32_t* val, uint8_t* state, uint64_t n, int algo,
-                                uint32_t source) {
+                                uint32_t source, const uint32_t* __restrict__ label0) {
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
-        val[v] = algo == ALG_CC ? (uint32_t)v : (v == source ? 0u : SERAPH_INF);
+        val[v] = algo == ALG_CC ? (label0 ? label0[v] : (uint32_t)v)
+                                : (v == source ? 0u : SERAPH_INF);
         if (state) state[v] = 0;
     }
 }
@@ -699,9 +703,23 @@ void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t 
     SR_LAUNCH();
 }
 
-void launch_init_values(int algo, const AlgoArgs& a, uint64_t n, uint32_t source, cudaStream_t s) {
+void launch_init_values(int algo, const AlgoArgs& a, uint64_t n, uint32_t source,
+                        const uint32_t* label0, cudaStream_t s) {
     if (algo == ALG_PR) return;  // PageRank init is done by launch_init_pr
-    init_min_kernel<<<grid_1d(n), kNT, 0, s>>>(a.val, a.state, n, algo, source);
+    init_min_kernel<<<grid_1d(n), kNT, 0, s>>>(a.val, a.state, n, algo, source, label0);
+    SR_LAUNCH();
+}
+
+__global__ void unpermute_kernel(const uint32_t* __restrict__ in, const uint32_t* __restrict__ inv,
+                                 uint64_t n, uint32_t* __restrict__ out) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x)
+        out[v] = in[inv[v]];
+}
+
+void launch_unpermute(const uint32_t* in, const uint32_t* inv, uint64_t n, uint32_t* out,
+                      cudaStream_t s) {
+    unpermute_kernel<<<grid_1d(n), kNT, 0, s>>>(in, inv, n, out);
     SR_LAUNCH();
 }
 

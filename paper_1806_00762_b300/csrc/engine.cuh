@@ -111,7 +111,10 @@ void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t 
                      const uint64_t* rel_soff, const uint64_t* rel_woff, const uint64_t* off_bytes,
                      uint8_t* sbase, uint8_t* wbase, RunState* rs, uint32_t seq, cudaStream_t s);
 void launch_init_values(int algo, const AlgoArgs& a, uint64_t n, uint32_t source,
-                        cudaStream_t s);
+                        const uint32_t* label0, cudaStream_t s);
+// out[v] = in[inv[v]]: values of a reordered graph back in the caller's ids.
+void launch_unpermute(const uint32_t* in, const uint32_t* inv, uint64_t n, uint32_t* out,
+                      cudaStream_t s);
 void launch_init_pr(const uint32_t* outdeg, const AlgoArgs& a, float* x_prev, uint64_t n,
                     cudaStream_t s);
 void launch_close_min(RunState* rs, SweepReport* out, cudaStream_t s);

@@ -38,6 +38,9 @@ struct seraph_graph {
     seraph::DevBuf<uint32_t> d_outdeg; // out-degree per vertex (PageRank)
     seraph::DevBuf<uint32_t> d_vb;     // page boundaries (u32) on the device
     seraph::DevBuf<uint32_t> d_zero_in; // bit v set: v has no in-edge
+    bool reordered = false;            // built with SERAPH_REORDER
+    seraph::DevBuf<uint32_t> d_perm;   // internal id -> caller's id (reordered only)
+    seraph::DevBuf<uint32_t> d_inv;    // caller's id -> internal id (reordered only)
 };
 
 namespace seraph {
@@ -54,8 +57,11 @@ struct Adjacency {
     DevBuf<uint8_t> wnar;   // weights if narrowed to 1 or 2 bytes
     const uint8_t* wptr() const { return wbytes < 4 ? wnar.p : (const uint8_t*)wcol.p; }
 };
+// perm/inv non-null: renumber vertices by non-increasing count in `lo`
+// (SERAPH_REORDER), perm = new -> old, inv = old -> new.
 void sorted_adjacency(uint64_t n, uint64_t m, const uint32_t* lo, const uint32_t* hi,
-                      const uint32_t* w, int mem, bool sym, cudaStream_t s, Adjacency& A);
+                      const uint32_t* w, int mem, bool sym, cudaStream_t s, Adjacency& A,
+                      DevBuf<uint32_t>* perm = nullptr, DevBuf<uint32_t>* inv = nullptr);
 void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src,
                  const uint32_t* dst, const uint32_t* w, int mem, uint32_t flags,
                  uint32_t num_pages, cudaStream_t s);

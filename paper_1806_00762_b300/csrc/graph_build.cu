@@ -430,6 +430,44 @@ __global__ void expand_csr_kernel(const uint64_t* __restrict__ row_off, uint64_t
     }
 }
 
+// Vertex keys for the out-degree order: (maxdeg - deg) above the id, so an
+// ascending sort gives non-increasing degree with ascending ids among ties.
+__global__ void vertex_key_kernel(const uint32_t* __restrict__ deg, uint64_t n, uint32_t maxdeg,
+                                  int b, uint64_t* __restrict__ keys) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x)
+        keys[v] = ((uint64_t)(maxdeg - deg[v]) << b) | v;
+}
+
+__global__ void perm_kernel(const uint64_t* __restrict__ keys, uint64_t n, int b,
+                            uint32_t* __restrict__ perm, uint32_t* __restrict__ inv) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = (uint32_t)(keys[i] & mask);
+        perm[i] = v;
+        inv[v] = (uint32_t)i;
+    }
+}
+
+__global__ void relabel_keys_kernel(const uint32_t* __restrict__ col, const uint32_t* __restrict__ dcol,
+                                    const uint32_t* __restrict__ inv, uint64_t E, int b,
+                                    uint64_t* __restrict__ keys) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E;
+         e += (uint64_t)gridDim.x * blockDim.x)
+        keys[e] = ((uint64_t)inv[dcol[e]] << b) | inv[col[e]];
+}
+
+__global__ void split_keys_kernel(const uint64_t* __restrict__ keys, uint64_t E, int b,
+                                  uint32_t* __restrict__ col, uint32_t* __restrict__ dcol) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        col[e] = (uint32_t)(keys[e] & mask);
+        dcol[e] = (uint32_t)(keys[e] >> b);
+    }
+}
+
 int bits_for(uint64_t n) {
     int b = 1;
     while (b < 64 && (1ull << b) < n) ++b;
@@ -444,6 +482,62 @@ const T* to_device(const T* p, uint64_t count, int mem, DevBuf<T>& hold, cudaStr
     return hold.p;
 }
 
+// Renumber the vertices of a deduplicated edge list (col = lo endpoint, dcol =
+// hi endpoint, sorted by (hi, lo)) in order of non-increasing occurrence count
+// in `col` -- the out-degree for the CSC -- ties by ascending id, and re-sort
+// the edges by (new hi, new lo).  perm: new -> old, inv: old -> new.
+void relabel_by_degree(uint64_t n, uint64_t E, int b, DevBuf<uint32_t>& col, DevBuf<uint32_t>& dcol,
+                       DevBuf<uint32_t>& wcol, bool weighted, DevBuf<uint32_t>& perm,
+                       DevBuf<uint32_t>& inv, cudaStream_t s) {
+    {
+        DevBuf<uint32_t> deg(n);
+        SR_CUDA(cudaMemsetAsync(deg.p, 0, n * sizeof(uint32_t), s));
+        if (E) {
+            outdeg_kernel<<<grid_for(E), kNT, 0, s>>>(col.p, E, deg.p);
+            SR_LAUNCH();
+        }
+        DevBuf<unsigned> mx(1);
+        SR_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned), s));
+        max_u32_kernel<<<grid_for(n), kNT, 0, s>>>(deg.p, n, mx.p);
+        SR_LAUNCH();
+        unsigned hmx = 0;
+        SR_CUDA(cudaMemcpyAsync(&hmx, mx.p, 4, cudaMemcpyDeviceToHost, s));
+        SR_CUDA(cudaStreamSynchronize(s));
+        DevBuf<uint64_t> vk(n), vk_alt(n);
+        vertex_key_kernel<<<grid_for(n), kNT, 0, s>>>(deg.p, n, hmx, b, vk.p);
+        SR_LAUNCH();
+        DevBuf<uint32_t> none, none_alt;
+        radix_sort(vk, vk_alt, none, none_alt, n, b + bits_for((uint64_t)hmx + 1), s);
+        perm.alloc(n);
+        inv.alloc(n);
+        perm_kernel<<<grid_for(n), kNT, 0, s>>>(vk.p, n, b, perm.p, inv.p);
+        SR_LAUNCH();
+        SR_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!E) return;
+    DevBuf<uint64_t> keys(E);
+    relabel_keys_kernel<<<grid_for(E), kNT, 0, s>>>(col.p, dcol.p, inv.p, E, b, keys.p);
+    SR_LAUNCH();
+    SR_CUDA(cudaStreamSynchronize(s));
+    col.release();
+    dcol.release();
+    DevBuf<uint64_t> keys_alt(E);
+    DevBuf<uint32_t> vals, vals_alt;
+    if (weighted) {
+        vals = std::move(wcol);
+        vals_alt.alloc(E);
+    }
+    radix_sort(keys, keys_alt, vals, vals_alt, E, 2 * b, s);
+    keys_alt.release();
+    vals_alt.release();
+    col.alloc(E);
+    dcol.alloc(E);
+    split_keys_kernel<<<grid_for(E), kNT, 0, s>>>(keys.p, E, b, col.p, dcol.p);
+    SR_LAUNCH();
+    if (weighted) wcol = std::move(vals);
+    SR_CUDA(cudaStreamSynchronize(s));
+}
+
 }  // namespace
 
 // Sorted, deduplicated adjacency of raw edges (lo -> hi): rows are the `hi`
@@ -452,7 +546,8 @@ const T* to_device(const T* p, uint64_t count, int mem, DevBuf<T>& hold, cudaStr
 // the out-edge CSR.  Self-loops are dropped, duplicates keep the smallest
 // weight, weights are narrowed to the smallest lossless width.
 void sorted_adjacency(uint64_t n, uint64_t m, const uint32_t* lo_in, const uint32_t* hi_in,
-                      const uint32_t* w_in, int mem, bool sym, cudaStream_t s, Adjacency& A) {
+                      const uint32_t* w_in, int mem, bool sym, cudaStream_t s, Adjacency& A,
+                      DevBuf<uint32_t>* perm, DevBuf<uint32_t>* inv) {
     const uint64_t M = sym ? 2 * m : m;
     const bool weighted = w_in != nullptr;
     const int b = bits_for(n);
@@ -511,6 +606,7 @@ void sorted_adjacency(uint64_t n, uint64_t m, const uint32_t* lo_in, const uint3
     }
     keys.release();
     vals.release();
+    if (perm) relabel_by_degree(n, E, b, col, dcol, wcol, weighted, *perm, *inv, s);
     A.E = E;
     // Narrowest lossless weight width (Sec. 3.1: the page format keeps the
     // transferred data as compact as possible).
@@ -547,9 +643,12 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     SR_CHECK(mem == SERAPH_MEM_HOST || mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad mem kind");
     SR_CHECK(m == 0 || (src_in && dst_in), SERAPH_EINVAL, "src/dst must not be NULL");
     SR_CHECK(m < (1ull << 36), SERAPH_EINVAL, "too many edges");
+    SR_CHECK((flags & ~(SERAPH_SYMMETRIZE | SERAPH_REORDER)) == 0, SERAPH_EINVAL, "unknown flag");
     const bool sym = flags & SERAPH_SYMMETRIZE;
+    const bool reorder = flags & SERAPH_REORDER;
     const bool weighted = w_in != nullptr;
     SR_CUDA(cudaGetDevice(&g->device));
+    g->reordered = reorder;
     g->n = n;
     g->m_raw = sym ? 2 * m : m;
     g->num_pages = P;
@@ -557,7 +656,8 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     g->symmetrized = sym;
 
     Adjacency A;
-    sorted_adjacency(n, m, src_in, dst_in, w_in, mem, sym, s, A);
+    sorted_adjacency(n, m, src_in, dst_in, w_in, mem, sym, s, A, reorder ? &g->d_perm : nullptr,
+                     reorder ? &g->d_inv : nullptr);
     const uint64_t E = A.E;
     g->m = E;
     g->wbytes = A.wbytes;

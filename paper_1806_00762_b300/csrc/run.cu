@@ -328,7 +328,10 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             launch_close_pr(a, n, x_prev.p, P->damping, partial.p, nparts, nullptr, cs.s);
             launches += 3;
         } else {
-            launch_init_values(algo, a, n, P->source, cs.s);
+            uint32_t source = P->source;
+            if (g->reordered && algo != SERAPH_CC)  // the caller's source id -> internal id
+                SR_CUDA(cudaMemcpy(&source, g->d_inv.p + source, 4, cudaMemcpyDeviceToHost));
+            launch_init_values(algo, a, n, source, g->reordered ? g->d_perm.p : nullptr, cs.s);
             launches += 1;
         }
         SR_CUDA(cudaStreamSynchronize(cs.s));
@@ -734,7 +737,18 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
 
     // ------------------------------------------------------------- output
     const void* src = is_pr ? (const void*)x.p : (const void*)val.p;
-    if (out) {
+    DevBuf<uint32_t> caller_order;
+    if (out && g->reordered) {  // back to the caller's vertex ids
+        uint32_t* dst = out_mem == SERAPH_MEM_DEVICE ? (uint32_t*)out : nullptr;
+        if (!dst) {
+            caller_order.alloc(n);
+            dst = caller_order.p;
+        }
+        launch_unpermute((const uint32_t*)src, g->d_inv.p, n, dst, cs.s);
+        ++launches;
+        src = dst;
+    }
+    if (out && src != out) {
         SR_CUDA(cudaMemcpyAsync(out, src, 4 * n,
                                 out_mem == SERAPH_MEM_HOST ? cudaMemcpyDeviceToHost
                                                            : cudaMemcpyDeviceToDevice,

@@ -1,0 +1,115 @@
+"""Graphs built with SERAPH_REORDER (vertices numbered internally by
+non-increasing out-degree): the internal order and the renumbered pages are
+bit-exact against the oracle's definition, and every result comes back in the
+caller's vertex ids, bit-exact (SSSP/BFS/CC) or within tolerance (PageRank),
+across schedules, prediction modes and output memories."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1806_00762_b300 as seraph
+from tests import graphs
+from tests.test_gpu_parity import PR_L1, PR_REL, budget, oracle_graph, pr_errors, rmat
+
+pytestmark = pytest.mark.gpu
+
+PART_CASES = [
+    ("rmat12-P7", lambda: rmat(12), 7, False),
+    ("rmat14-sym-P16", lambda: rmat(14, weighted=False), 16, True),
+    ("random-P64", lambda: (300,) + graphs.random_graph(300, 5000, seed=5), 64, False),
+    ("tiny-P16", lambda: (5,) + graphs.random_graph(5, 12, seed=1), 16, False),
+    ("noedges", lambda: (9, np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.uint32)), 3, False),
+]
+
+
+@pytest.mark.parametrize("name,make,P,sym", PART_CASES, ids=[c[0] for c in PART_CASES])
+def test_reordered_partition_matches_oracle(name, make, P, sym):
+    n, src, dst, w = make()
+    g = seraph.Graph.from_edges(n, src, dst, w, symmetrize=sym, num_pages=P, reorder=True)
+    og = oracle_graph(n, src, dst, w, symmetrize=sym)
+    perm = oracle.degree_order(og)
+    assert g.info()["reordered"] == 1
+    assert np.array_equal(g.perm(), perm)
+    h = oracle.relabel(og, perm)
+    ocol_off, orow, ow = oracle.csc(h)
+    col_off, row, wc, od = g.export_csc()
+    assert np.array_equal(col_off, ocol_off)
+    assert np.array_equal(row, orow)
+    if w is not None:
+        assert np.array_equal(wc, ow)
+    assert np.array_equal(od, h.out_degree().astype(np.uint32))
+    assert np.array_equal(g.page_bounds(), oracle.page_cut(n, ocol_off, P))
+
+
+def test_identity_order_without_the_flag():
+    n, src, dst, w = rmat(10)
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=3)
+    assert g.info()["reordered"] == 0
+    assert np.array_equal(g.perm(), np.arange(n, dtype=np.uint32))
+
+
+@pytest.fixture(scope="module")
+def r13r():
+    n, src, dst, w = rmat(13)
+    og = oracle_graph(n, src, dst, w)
+    ogs = oracle_graph(n, src, dst, None, symmetrize=True)
+    return dict(n=n, g=seraph.Graph.from_edges(n, src, dst, w, num_pages=48, reorder=True),
+                gs=seraph.Graph.from_edges(n, src, dst, None, symmetrize=True, num_pages=48,
+                                           reorder=True),
+                sssp=oracle.sssp(og, 5), bfs=oracle.bfs(og, 5), cc=oracle.cc(ogs),
+                pr=oracle.pagerank(og)[0])
+
+
+SCHEDULES = [
+    dict(window=1, passes=1, order="cyclic", slots=16, pvu="strong"),   # the benchmark's SSSP form
+    dict(window=1, passes=1, order="zigzag", slots=16, pvu="weak"),     # the benchmark's PageRank form
+    dict(window=4, passes=1, order="cyclic", pvu="weak"),               # the paper's plain form
+    dict(window=2, passes=3, order="zigzag", max_passes=6),
+    dict(window=1, passes=1, thread_max_deg=0, group4_max_deg=0, group8_max_deg=0,
+         warp_max_deg=0),
+]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES, ids=lambda s: "-".join(f"{k}{v}" for k, v in s.items()))
+@pytest.mark.parametrize("algo", ["sssp", "bfs", "cc", "pagerank"])
+def test_reordered_results_in_caller_ids(r13r, algo, sched):
+    g = r13r["gs"] if algo == "cc" else r13r["g"]
+    kw = dict(sched)
+    nslot = kw.get("slots", kw["window"] + 1)
+    kw["budget_bytes"] = budget(g, nslot - 1, 1.7, algo == "sssp")
+    if algo == "pagerank" and kw.get("pvu") == "strong":
+        kw["pvu"] = "weak"  # Table 1 gives PageRank no strong condition
+    got, st = seraph.run(g, algo, source=5, **kw)
+    assert st["converged"] == 1
+    if algo == "pagerank":
+        l1, rel = pr_errors(got, r13r["pr"])
+        assert l1 <= PR_L1 and rel <= PR_REL, (l1, rel)
+    else:
+        assert np.array_equal(got, r13r[algo])
+
+
+@pytest.mark.parametrize("algo", ["sssp", "cc", "pagerank"])
+def test_reordered_output_to_device(r13r, algo):
+    import torch
+    g = r13r["gs"] if algo == "cc" else r13r["g"]
+    out = torch.empty(r13r["n"], dtype=torch.float32 if algo == "pagerank" else torch.int32,
+                      device="cuda")
+    seraph.run(g, algo, out=out, source=5, window=2,
+               budget_bytes=budget(g, 2, 1.7, algo == "sssp"))
+    got = out.cpu().numpy()
+    if algo == "pagerank":
+        l1, rel = pr_errors(got, r13r["pr"])
+        assert l1 <= PR_L1 and rel <= PR_REL
+    else:
+        assert np.array_equal(got.view(np.uint32), r13r[algo])
+
+
+def test_reordered_csr_input_and_every_source():
+    n, src, dst, w = rmat(9)
+    og = oracle_graph(n, src, dst, w)
+    g = seraph.Graph.from_csr(n, og.row_off, og.col, og.w, num_pages=5, reorder=True)
+    assert np.array_equal(g.perm(), oracle.degree_order(og))
+    for s in range(0, n, 37):
+        d, _ = seraph.run(g, "sssp", source=s, window=2, budget_bytes=budget(g, 2, 1.7))
+        assert np.array_equal(d, oracle.sssp(og, s)), s

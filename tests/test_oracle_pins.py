@@ -122,6 +122,42 @@ def test_page_cut_definition(P):
         assert vb[j] == want
 
 
+def test_degree_order_worked_example():
+    """Out-degrees (kept edges) 0:1 1:3 2:0 3:3 4:1 5:2 -- the self-loop 2->2
+    and the duplicate 1->2 do not count -- so the order is 1, 3 (degree 3, by
+    id), 5, 0, 4 (degree 1, by id), 2."""
+    src = np.array([0, 1, 1, 1, 1, 2, 3, 3, 3, 4, 5, 5], np.uint32)
+    dst = np.array([1, 0, 2, 2, 3, 2, 0, 1, 5, 0, 0, 4], np.uint32)
+    g = oracle.build_csr(6, src, dst)
+    assert list(oracle.degree_order(g)) == [1, 3, 5, 0, 4, 2]
+
+
+def test_degree_order_by_brute_force_and_relabel_is_an_isomorphism():
+    for seed in range(6):
+        n = 40
+        src, dst, w = graphs.random_graph(n, 160, seed=seed)
+        g = oracle.build_csr(n, src, dst, w)
+        perm = oracle.degree_order(g)
+        deg = [sum(1 for u, v in set(zip(src.tolist(), dst.tolist())) if u == x and u != v)
+               for x in range(n)]
+        # brute force: position of x = vertices that must precede it
+        for x in range(n):
+            before = sum(1 for y in range(n) if deg[y] > deg[x] or (deg[y] == deg[x] and y < x))
+            assert perm[before] == x
+        h = oracle.relabel(g, perm)
+        inv = np.empty(n, np.int64)
+        inv[perm] = np.arange(n)
+        assert h.m == g.m
+        edges_g = {(int(inv[u]), int(v_), int(c)) for u in range(n)
+                   for v_, c in zip(inv[g.col[g.row_off[u]:g.row_off[u + 1]]],
+                                    g.w[g.row_off[u]:g.row_off[u + 1]])}
+        edges_h = {(u, int(v_), int(c)) for u in range(n)
+                   for v_, c in zip(h.col[h.row_off[u]:h.row_off[u + 1]],
+                                    h.w[h.row_off[u]:h.row_off[u + 1]])}
+        assert edges_g == edges_h
+        assert np.all(np.diff(h.out_degree().astype(np.int64)) <= 0)
+
+
 # ------------------------------------------------------------------ SSSP
 
 def floyd_warshall(n, src, dst, w):
