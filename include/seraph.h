@@ -209,7 +209,18 @@ typedef struct seraph_params {
     void*    sched_model;       /* seraph_sched_model* for SERAPH_SCHED_LEARNED */
     void*    stream;            /* cudaStream_t for compute, NULL = own       */
     void*    trace;             /* seraph_trace* to fill, or NULL             */
+    uint64_t l2_hot_bytes;      /* L2 residency hint (not in the paper): the
+                                   gathered values of vertices with internal
+                                   id < l2_hot_bytes / 4 are read with L2
+                                   evict-last priority and streamed page data
+                                   with evict-first, so the most-read values
+                                   stay in L2 (pair with SERAPH_REORDER, which
+                                   puts them first).  0 = no hints; the
+                                   default SERAPH_L2_HOT_AUTO = half the
+                                   device's L2.  Never changes a result.      */
 } seraph_params;
+
+#define SERAPH_L2_HOT_AUTO UINT64_MAX
 
 typedef struct seraph_stats {
     uint32_t sweeps;            /* sweeps run                                 */

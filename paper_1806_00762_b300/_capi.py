@@ -60,7 +60,7 @@ class Params(ctypes.Structure):
                 ("sched", i32), ("timeout_ms", u32), ("profile", u32), ("order", u32),
                 ("max_passes", u32), ("slots", u32), ("group4_max_deg", u32),
                 ("group8_max_deg", u32),
-                ("sched_model", vp), ("stream", vp), ("trace", vp)]
+                ("sched_model", vp), ("stream", vp), ("trace", vp), ("l2_hot_bytes", u64)]
 
 
 class Stats(ctypes.Structure):

@@ -190,6 +190,7 @@ int seraph_params_default(seraph_params* p, int algo) {
         p->warp_max_deg = 4096;
         p->sched = SERAPH_SCHED_FIXED;
         p->timeout_ms = 600000;
+        p->l2_hot_bytes = SERAPH_L2_HOT_AUTO;
         return SERAPH_OK;
     });
 }

@@ -26,41 +26,71 @@ constexpr int kNT = 256;
 constexpr int kCompactRounds = 4;
 constexpr uint32_t kCompactTile = kNT * kCompactRounds;
 
+// L2 eviction-priority policies (createpolicy, sm_80+).  Page data of the
+// resident chunk is read once per pass (evict-first); the gathered values of
+// the lowest-numbered `hot` vertices -- the most-read ones once vertices are
+// numbered by out-degree -- are kept (evict-last).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Streaming loads of the resident chunk (read-only while a pass runs; not
 // kept in L1).  Not volatile: the compiler may batch them for more loads in
 // flight.
-__device__ __forceinline__ uint4 ld_stream4(const void* p) {
+__device__ __forceinline__ uint4 ld_stream4(const void* p, uint64_t pol) {
     uint4 r;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
         : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p));
+        : "l"(p), "l"(pol));
     return r;
 }
 
-__device__ __forceinline__ uint2 ld_stream2(const void* p) {
+__device__ __forceinline__ uint2 ld_stream2(const void* p, uint64_t pol) {
     uint2 r;
-    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+        : "=r"(r.x), "=r"(r.y)
+        : "l"(p), "l"(pol));
     return r;
 }
 
-__device__ __forceinline__ uint32_t ld_stream(const void* p) {
+__device__ __forceinline__ uint32_t ld_stream(const void* p, uint64_t pol) {
     uint32_t r;
-    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    return r;
+}
+
+// Gathered source value (weak load: values may change during a pass).
+__device__ __forceinline__ uint32_t ld_gather(const void* p, uint64_t pol) {
+    uint32_t r;
+    asm("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
     return r;
 }
 
 // Four weights of edges idx..idx+3 (idx a multiple of 4) stored WB bytes wide.
 template <int WB>
-__device__ __forceinline__ void ld_weights4(const uint8_t* w, uint32_t idx, uint32_t out[4]) {
+__device__ __forceinline__ void ld_weights4(const uint8_t* w, uint32_t idx, uint32_t out[4],
+                                            uint64_t pol) {
     if (WB == 1) {
-        const uint32_t v = ld_stream(w + idx);
+        const uint32_t v = ld_stream(w + idx, pol);
 #pragma unroll
         for (int k = 0; k < 4; ++k) out[k] = (v >> (8 * k)) & 0xFFu;
     } else if (WB == 2) {
-        const uint2 v = ld_stream2(w + 2 * (uint64_t)idx);
+        const uint2 v = ld_stream2(w + 2 * (uint64_t)idx, pol);
         out[0] = v.x & 0xFFFFu; out[1] = v.x >> 16; out[2] = v.y & 0xFFFFu; out[3] = v.y >> 16;
     } else {
-        const uint4 v = ld_stream4(w + 4 * (uint64_t)idx);
+        const uint4 v = ld_stream4(w + 4 * (uint64_t)idx, pol);
         out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
     }
 }
@@ -173,18 +203,22 @@ __device__ __forceinline__ void gather8(const AlgoArgs& a, const PageLoc& loc, u
                                         uint32_t e, uint32_t idx0, uint32_t idx1, MinAcc& macc,
                                         SumAcc& sacc) {
     const bool two = idx1 < e;
-    const uint4 c0 = ld_stream4(loc.col + idx0);
-    const uint4 c1 = two ? ld_stream4(loc.col + idx1) : make_uint4(0, 0, 0, 0);
+    const uint64_t pn = policy_evict_normal();
+    const uint64_t ps = a.hints ? policy_evict_first() : pn;
+    const uint64_t ph = a.hints ? policy_evict_last() : pn;
+    const uint4 c0 = ld_stream4(loc.col + idx0, ps);
+    const uint4 c1 = two ? ld_stream4(loc.col + idx1, ps) : make_uint4(0, 0, 0, 0);
     uint32_t w[8] = {1, 1, 1, 1, 1, 1, 1, 1};
     if (ALGO == ALG_SSSP) {
-        ld_weights4<WB>(loc.w, idx0, w);
-        if (two) ld_weights4<WB>(loc.w, idx1, w + 4);
+        ld_weights4<WB>(loc.w, idx0, w, ps);
+        if (two) ld_weights4<WB>(loc.w, idx1, w + 4, ps);
     }
     const uint32_t cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
     if (ALGO == ALG_PR) {
         float g[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) g[j] = a.contrib[cc[j]];
+        for (int j = 0; j < 8; ++j)
+            g[j] = __uint_as_float(ld_gather(a.contrib + cc[j], cc[j] < a.hot ? ph : pn));
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const uint32_t i = (j < 4 ? idx0 : idx1) + (j & 3);
@@ -193,7 +227,7 @@ __device__ __forceinline__ void gather8(const AlgoArgs& a, const PageLoc& loc, u
     } else {
         uint32_t g[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) g[j] = a.val[cc[j]];
+        for (int j = 0; j < 8; ++j) g[j] = ld_gather(a.val + cc[j], cc[j] < a.hot ? ph : pn);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const uint32_t i = (j < 4 ? idx0 : idx1) + (j & 3);

@@ -87,7 +87,8 @@ struct AlgoArgs {
     uint8_t skip_mask;
     uint8_t pvu;              // SERAPH_PVU_*
     uint8_t wbytes;           // stored weight width: 1, 2 or 4 bytes
-    uint8_t pad;
+    uint8_t hints;            // 1: L2 eviction-priority hints on (see hot)
+    uint32_t hot;             // gathers of vertices < hot: L2 evict-last
 };
 
 // Launchers (engine.cu).  `pass` is the global pass counter (its parity picks

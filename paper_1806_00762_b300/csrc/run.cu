@@ -316,6 +316,16 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     a.skip_mask = P->fsm_skip_mask;
     a.pvu = (uint8_t)P->pvu;
     a.wbytes = (uint8_t)g->wbytes;
+    {
+        uint64_t hot_bytes = P->l2_hot_bytes;
+        if (hot_bytes == SERAPH_L2_HOT_AUTO) {
+            int l2 = 0;
+            SR_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device));
+            hot_bytes = (uint64_t)l2 / 2;
+        }
+        a.hints = hot_bytes > 0;
+        a.hot = (uint32_t)std::min<uint64_t>(n, hot_bytes / 4);
+    }
 
     uint64_t launches = 0;
     {
