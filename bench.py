@@ -48,9 +48,9 @@ def parse():
     ap.add_argument("--scale", type=int, default=28)
     ap.add_argument("--pages", type=int, default=512)
     ap.add_argument("--budget-gb", type=float, default=16.0)
-    ap.add_argument("--sssp", default="order=cyclic,window=1,slots=16,pvu=strong",
+    ap.add_argument("--sssp", default="order=cyclic,window=1,slots=32,pvu=strong,verify=0",
                     help="SSSP schedule: comma-separated seraph_params overrides")
-    ap.add_argument("--pagerank", default="order=zigzag,window=1,slots=16,pvu=weak",
+    ap.add_argument("--pagerank", default="order=zigzag,window=1,slots=32,pvu=weak",
                     help="PageRank schedule: comma-separated seraph_params overrides")
     ap.add_argument("--vertex-order", default="degree", choices=["degree", "natural"],
                     help="degree: vertices numbered by non-increasing out-degree before the "

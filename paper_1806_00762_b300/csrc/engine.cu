@@ -160,34 +160,60 @@ struct Locals {
     unsigned long long edges;
 };
 
+__device__ __forceinline__ uint8_t fsm_next(const AlgoArgs& a, uint32_t st, uint32_t c) {
+    return (uint8_t)((a.fsm_bits >> (3 * (2 * st + c))) & 7u);
+}
+
 __device__ __forceinline__ uint8_t fsm_step(const AlgoArgs& a, uint8_t st, bool ch) {
     // A dormant state reached here only because prediction is off for the
     // pass: a valid update follows its "changed" edge, otherwise it keeps its
     // state (its ticks belong to predicted passes).
-    if ((a.skip_mask >> st) & 1) return ch ? a.fsm_next[2 * st + 1] : st;
-    return a.fsm_next[2 * st + (ch ? 1 : 0)];
+    if ((a.skip_mask >> st) & 1) return ch ? fsm_next(a, st, 1) : st;
+    return fsm_next(a, st, ch ? 1 : 0);
+}
+
+// The vertex's own value and prediction state, loaded when its processing
+// starts so that their latency overlaps the gathers (only the thread
+// processing v in this pass writes them).
+struct Own {
+    uint32_t old;  // SSSP/BFS/CC value
+    float xo;      // PageRank value
+    uint8_t st;    // weak-prediction state
+};
+
+template <int ALGO>
+__device__ __forceinline__ Own load_own(const AlgoArgs& a, uint32_t v) {
+    Own o{0u, 0.f, 0};
+    if (ALGO == ALG_PR) o.xo = a.x[v];
+    else o.old = a.val[v];
+    if (a.pvu == SERAPH_PVU_WEAK) o.st = a.state[v];
+    return o;
 }
 
 template <int ALGO>
 __device__ __forceinline__ void finish_min(const AlgoArgs& a, uint32_t v, const MinAcc& acc,
-                                           uint32_t deg, Locals& L) {
-    uint32_t old = a.val[v];
-    bool ch = acc.best < old;
+                                           uint32_t deg, Locals& L, const Own& o) {
+    bool ch = acc.best < o.old;
     if (ch) a.val[v] = acc.best;
-    if (ALGO == ALG_SSSP && acc.ovf && acc.best == SERAPH_INF && old == SERAPH_INF) L.ovf = 1;
-    if (a.pvu == SERAPH_PVU_WEAK) a.state[v] = fsm_step(a, a.state[v], ch);
+    if (ALGO == ALG_SSSP && acc.ovf && acc.best == SERAPH_INF && o.old == SERAPH_INF) L.ovf = 1;
+    if (a.pvu == SERAPH_PVU_WEAK) {
+        const uint8_t ns = fsm_step(a, o.st, ch);
+        if (ns != o.st) a.state[v] = ns;
+    }
     L.changed += ch;
     L.edges += deg;
     if (ch) L.minv = min(L.minv, acc.best);
 }
 
 __device__ __forceinline__ void finish_pr(const AlgoArgs& a, uint32_t v, float sum, float base,
-                                          uint32_t deg, Locals& L) {
-    float xo = a.x[v];
+                                          uint32_t deg, Locals& L, const Own& o) {
     float xn = base + a.damping * sum;
     a.x_next[v] = xn;
-    bool ch = fabsf(xn - xo) > a.fail_eps * xo;
-    if (a.pvu == SERAPH_PVU_WEAK) a.state[v] = fsm_step(a, a.state[v], ch);
+    bool ch = fabsf(xn - o.xo) > a.fail_eps * o.xo;
+    if (a.pvu == SERAPH_PVU_WEAK) {
+        const uint8_t ns = fsm_step(a, o.st, ch);
+        if (ns != o.st) a.state[v] = ns;
+    }
     L.changed += ch;
     L.edges += deg;
 }
@@ -251,13 +277,14 @@ __device__ __forceinline__ void vertex_thread(const AlgoArgs& a, unsigned long l
     const uint32_t v = (uint32_t)ent, p = (uint32_t)(ent >> 32);
     const PageLoc loc = a.loc[p];
     const uint32_t li = v - loc.vb;
+    const Own own = load_own<ALGO>(a, v);
     const uint32_t b = loc.off[li], e = loc.off[li + 1];
     MinAcc macc{SERAPH_INF, false};
     SumAcc sacc{0.f, 0.f};
     for (uint32_t idx = b & ~3u; idx < e; idx += 8)
         gather8<ALGO, KAHAN, WB>(a, loc, b, e, idx, idx + 4, macc, sacc);
-    if (ALGO == ALG_PR) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L);
-    else finish_min<ALGO>(a, v, macc, e - b, L);
+    if (ALGO == ALG_PR) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L, own);
+    else finish_min<ALGO>(a, v, macc, e - b, L, own);
 }
 
 // Group of G lanes (G = 32: a warp; G = CTA size for hubs).  Lane t reads the
@@ -283,8 +310,10 @@ __device__ __forceinline__ void vertex_group(const AlgoArgs& a, unsigned long lo
     MinAcc macc{SERAPH_INF, false};
     SumAcc sacc{0.f, 0.f};
     uint32_t v = 0, b = 0, e = 0;
+    Own own{0u, 0.f, 0};
     if (valid) {
         v = (uint32_t)ent;
+        if (t == 0) own = load_own<ALGO>(a, v);
         const PageLoc loc = a.loc[(uint32_t)(ent >> 32)];
         const uint32_t li = v - loc.vb;
         b = loc.off[li];
@@ -297,14 +326,14 @@ __device__ __forceinline__ void vertex_group(const AlgoArgs& a, unsigned long lo
             SumAcc other{__shfl_xor_sync(kFull, sacc.s, o), __shfl_xor_sync(kFull, sacc.c, o)};
             sacc = (t & o) ? sum_merge<KAHAN>(other, sacc) : sum_merge<KAHAN>(sacc, other);
         }
-        if (valid && t == 0) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L);
+        if (valid && t == 0) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L, own);
     } else {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             macc.best = min(macc.best, __shfl_xor_sync(kFull, macc.best, o));
             macc.ovf |= __shfl_xor_sync(kFull, (int)macc.ovf, o) != 0;
         }
-        if (valid && t == 0) finish_min<ALGO>(a, v, macc, e - b, L);
+        if (valid && t == 0) finish_min<ALGO>(a, v, macc, e - b, L, own);
     }
 }
 
@@ -317,6 +346,8 @@ __device__ __forceinline__ void vertex_cta(const AlgoArgs& a, unsigned long long
     const uint32_t li = v - loc.vb;
     const uint32_t b = loc.off[li], e = loc.off[li + 1];
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    Own own{0u, 0.f, 0};
+    if (threadIdx.x == 0) own = load_own<ALGO>(a, v);
     MinAcc macc{SERAPH_INF, false};
     SumAcc sacc{0.f, 0.f};
     edges_strided<ALGO, KAHAN, WB>(a, loc, b, e, threadIdx.x, kNT, macc, sacc);
@@ -331,7 +362,7 @@ __device__ __forceinline__ void vertex_cta(const AlgoArgs& a, unsigned long long
         if (threadIdx.x == 0) {
             SumAcc t{s_sum[0], s_comp[0]};
             for (int w = 1; w < kNT / 32; ++w) t = sum_merge<KAHAN>(t, SumAcc{s_sum[w], s_comp[w]});
-            finish_pr(a, v, t.s - t.c, base, e - b, L);
+            finish_pr(a, v, t.s - t.c, base, e - b, L, own);
         }
     } else {
         macc.best = __reduce_min_sync(kFull, macc.best);
@@ -341,7 +372,7 @@ __device__ __forceinline__ void vertex_cta(const AlgoArgs& a, unsigned long long
         if (threadIdx.x == 0) {
             MinAcc t{s_min[0], s_ovf[0] != 0};
             for (int w = 1; w < kNT / 32; ++w) { t.best = min(t.best, s_min[w]); t.ovf |= s_ovf[w] != 0; }
-            finish_min<ALGO>(a, v, t, e - b, L);
+            finish_min<ALGO>(a, v, t, e - b, L, own);
         }
     }
     __syncthreads();
@@ -424,7 +455,7 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
                     const uint8_t st = a.state[v];
                     if ((a.skip_mask >> st) & 1) {
                         skip = true;
-                        a.state[v] = a.fsm_next[2 * st];  // dormant tick
+                        a.state[v] = fsm_next(a, st, 0);  // dormant tick
                     }
                 }
                 if (skip) {
@@ -485,8 +516,11 @@ __device__ __forceinline__ void group_phase(const AlgoArgs& a, int par, int k, f
     }
 }
 
+// Six CTAs per SM (<= 42 registers) keep enough warps in flight for the
+// gathers (PageRank's compensated sums would otherwise take 48); SSSP's
+// weights need more registers, five CTAs (<= 51).
 template <int ALGO, bool KAHAN, int WB>
-__global__ void __launch_bounds__(kNT)
+__global__ void __launch_bounds__(kNT, ALGO == ALG_SSSP ? 5 : 6)
     relax_kernel(AlgoArgs a, uint32_t pass, uint32_t step) {
     __shared__ unsigned s_item;
     __shared__ float s_sum[kNT / 32], s_comp[kNT / 32];

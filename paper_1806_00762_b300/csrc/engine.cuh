@@ -83,7 +83,7 @@ struct AlgoArgs {
     uint32_t step_mask;           // ring size - 1
     uint32_t cls_max[4];      // largest in-degree of classes 0..3 (above: class 4)
     float damping, fail_eps;
-    uint8_t fsm_next[12];
+    uint64_t fsm_bits;        // next state of (state s, changed c) in bits 3(2s+c)..+2
     uint8_t skip_mask;
     uint8_t pvu;              // SERAPH_PVU_*
     uint8_t wbytes;           // stored weight width: 1, 2 or 4 bytes

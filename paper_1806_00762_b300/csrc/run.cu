@@ -312,7 +312,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     a.cls_max[3] = P->warp_max_deg;
     a.damping = (float)P->damping;
     a.fail_eps = (float)P->pr_fail_eps;
-    std::memcpy(a.fsm_next, P->fsm_next, 12);
+    a.fsm_bits = 0;
+    for (int i = 0; i < 12; ++i) a.fsm_bits |= (uint64_t)P->fsm_next[i] << (3 * i);
     a.skip_mask = P->fsm_skip_mask;
     a.pvu = (uint8_t)P->pvu;
     a.wbytes = (uint8_t)g->wbytes;
@@ -730,7 +731,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             // SSSP/BFS/CC: skip chunks predicted to change nothing, except after
             // a sweep without changes and at least every fourth sweep (the
             // stop rule needs every chunk processed after the last change)
-            const bool may_skip = !is_pr && rep.changed > 0 && skip_streak < 3;
+            // (never without the prediction-off check: a skipped chunk breaks
+            // the every-chunk-every-sweep premise of the strong conditions)
+            const bool may_skip = !is_pr && P->verify && rep.changed > 0 && skip_streak < 3;
             if (may_skip) {
                 std::vector<uint32_t> keep;
                 for (uint32_t c : ord)

@@ -235,13 +235,20 @@ def test_pagerank_streamed(r13_paged, sched):
     assert l1 <= PR_L1 and rel <= PR_REL, (l1, rel, st)
 
 
+STRONG_ALONE = [dict(window=2), dict(window=1, slots=32), dict(window=1, slots=7, order="zigzag"),
+                dict(window=3, passes=2, order="zigzag"), dict(window=1, slots=6, max_passes=4)]
+
+
+@pytest.mark.parametrize("sched", STRONG_ALONE, ids=lambda s: "-".join(f"{k}{v}" for k, v in s.items()))
 @pytest.mark.parametrize("algo", ["sssp", "bfs", "cc"])
-def test_strong_prediction_alone_is_exact(r13_paged, algo):
+def test_strong_prediction_alone_is_exact(r13_paged, algo, sched):
     """Strong conditions of Table 1 (as read for asynchronous sweeps) without
-    the final prediction-off sweep still give the exact fixpoint."""
+    the final prediction-off sweep still give the exact fixpoint, in every
+    schedule that processes every chunk in every sweep."""
     g = r13_paged["gs"] if algo == "cc" else r13_paged["g"]
-    got, st = seraph.run(g, algo, source=5, window=2, pvu="strong", verify=0,
-                         budget_bytes=budget(g, 2, 1.7, algo == "sssp"))
+    kw = dict(sched)
+    kw["budget_bytes"] = budget(g, kw.get("slots", kw["window"] + 1) - 1, 1.7, algo == "sssp")
+    got, st = seraph.run(g, algo, source=5, pvu="strong", verify=0, **kw)
     assert np.array_equal(got, r13_paged[algo])
     assert st["vertices_skipped"] > 0
 
