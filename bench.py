@@ -48,9 +48,9 @@ def parse():
     ap.add_argument("--scale", type=int, default=28)
     ap.add_argument("--pages", type=int, default=512)
     ap.add_argument("--budget-gb", type=float, default=16.0)
-    ap.add_argument("--sssp", default="order=cyclic,window=1,slots=32,pvu=strong,verify=0",
+    ap.add_argument("--sssp", default="order=cyclic,window=1,slots=32,pvu=strong,verify=0,columns=packed",
                     help="SSSP schedule: comma-separated seraph_params overrides")
-    ap.add_argument("--pagerank", default="order=zigzag,window=1,slots=32,pvu=weak",
+    ap.add_argument("--pagerank", default="order=zigzag,window=1,slots=32,pvu=weak,columns=plain",
                     help="PageRank schedule: comma-separated seraph_params overrides")
     ap.add_argument("--vertex-order", default="degree", choices=["degree", "natural"],
                     help="degree: vertices numbered by non-increasing out-degree before the "
@@ -135,7 +135,7 @@ def link_gbps(torch, nbytes=1 << 30, reps=5, chunks=4) -> float:
     return chunks * nbytes / (best / 1e3) / 1e9
 
 
-def build_graph(seraph, synth, torch, scale, pages, reorder=True):
+def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True):
     n = 1 << scale
     m = synth.rmat_config(scale).m
     src = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -143,7 +143,7 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True):
     w = torch.empty_like(src)
     synth.rmat_edges_device(scale, src.data_ptr(), dst.data_ptr(), w.data_ptr())
     torch.cuda.synchronize()
-    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=pages, reorder=reorder)
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=pages, reorder=reorder, compress=compress)
     del src, dst, w
     torch.cuda.empty_cache()
     return g
@@ -153,7 +153,7 @@ def parse_sched(text: str) -> dict:
     out = {}
     for item in filter(None, text.split(",")):
         k, v = item.split("=")
-        out[k.strip()] = v.strip() if k.strip() in ("order", "pvu") else int(v)
+        out[k.strip()] = v.strip() if k.strip() in ("order", "pvu", "columns") else int(v)
     return out
 
 
@@ -419,7 +419,7 @@ def main():
         "wall_s_timed": wall,
     }
     if not args.no_paper_schedule:
-        plain = dict(order="cyclic", window=4, slots=5, pvu="weak")
+        plain = dict(order="cyclic", window=4, slots=5, pvu="weak", columns="plain")
         p1, p2 = step(plain, plain)
         line["paper_schedule"] = {
             "schedule": plain, "time_to_fixpoint_s": {"sssp": p1["time_ms"] / 1e3,

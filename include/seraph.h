@@ -75,6 +75,16 @@ enum seraph_order { SERAPH_ORDER_CYCLIC = 0, SERAPH_ORDER_ZIGZAG = 1 };
                                  labels stay in the caller's ids; only the
                                  page contents (export_csc, page_bounds) are
                                  in internal ids (see seraph_graph_export_perm) */
+#define SERAPH_COMPRESS   4u  /* also keep every page in a packed form: per
+                                 destination its first source id, then each
+                                 gap to the next source minus one, as LEB128
+                                 bytes (7 bits per byte, low group first, high
+                                 bit set on all but a value's last byte), with
+                                 u32 page-relative byte offsets per vertex
+                                 beside the u32 edge offsets.  A lossless
+                                 encoding of the compact page of Sec. 3.1 that
+                                 streams ~2 bytes per edge instead of 4; runs
+                                 pick the form with seraph_params.columns    */
 
 typedef struct seraph_graph seraph_graph;  /* opaque, library-owned */
 
@@ -94,6 +104,11 @@ typedef struct seraph_graph_info {
     uint32_t weight_width;      /* bytes per stored weight: 1, 2 or 4 (the
                                    narrowest that holds the largest weight) */
     uint32_t reordered;         /* 1 if built with SERAPH_REORDER            */
+    uint32_t packed;            /* 1 if built with SERAPH_COMPRESS           */
+    uint32_t reserved;
+    uint64_t packed_bytes;      /* pinned bytes of all packed page structures */
+    uint64_t packed_data_bytes; /* gap-stream bytes of all pages (unpadded)  */
+    uint64_t max_page_packed_bytes;
 } seraph_graph_info;
 
 /*
@@ -140,6 +155,11 @@ int  seraph_graph_export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t*
  * out-degrees and perm[i] < perm[j]; out-degrees count kept edges (after
  * SYMMETRIZE, self-loop removal and deduplication). */
 int  seraph_graph_export_perm(const seraph_graph* g, uint32_t* perm);
+
+/* The packed gap streams (SERAPH_COMPRESS graphs; SERAPH_EINVAL otherwise),
+ * pages concatenated without padding: boff[n+1] global byte offsets of each
+ * destination's bytes, data[packed_data_bytes].  Either may be NULL. */
+int  seraph_graph_export_packed(const seraph_graph* g, uint64_t* boff, uint8_t* data);
 
 void seraph_graph_free(seraph_graph* g);
 
@@ -209,6 +229,10 @@ typedef struct seraph_params {
     void*    sched_model;       /* seraph_sched_model* for SERAPH_SCHED_LEARNED */
     void*    stream;            /* cudaStream_t for compute, NULL = own       */
     void*    trace;             /* seraph_trace* to fill, or NULL             */
+    uint32_t columns;           /* page form streamed: SERAPH_COLUMNS_AUTO
+                                   (packed when the graph has it), _PLAIN (u32
+                                   source ids) or _PACKED (LEB128 gaps)      */
+    uint32_t pad1;
     uint64_t l2_hot_bytes;      /* L2 residency hint (not in the paper): the
                                    gathered values of vertices with internal
                                    id < l2_hot_bytes / 4 are read with L2
@@ -221,6 +245,9 @@ typedef struct seraph_params {
 } seraph_params;
 
 #define SERAPH_L2_HOT_AUTO UINT64_MAX
+#define SERAPH_COLUMNS_AUTO   0u
+#define SERAPH_COLUMNS_PLAIN  1u
+#define SERAPH_COLUMNS_PACKED 2u
 
 typedef struct seraph_stats {
     uint32_t sweeps;            /* sweeps run                                 */

@@ -9,8 +9,9 @@ The C part (``oracle.c``) writes out the plain definitions: Dijkstra, FIFO
 BFS, union-find weakly-connected components and FP64 PageRank power iteration
 (evaluation section "Graph Algorithms"; Sec. 4.3 for PageRank), the CSR/CSC
 build and the destination-range page cut (Sec. 3.1 "Subgraph Organization"),
-and the out-degree vertex order (``degree_order``; a layout outside the
-paper that renames vertices only).
+the out-degree vertex order (``degree_order``; a layout outside the paper
+that renames vertices only) and the packed page columns (``pack_gaps``;
+LEB128 gaps, a lossless encoding outside the paper).
 ``mlp.py`` holds the FP64 reference of the learned scheduler's network.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
@@ -150,6 +151,64 @@ def relabel(g: CSR, perm) -> CSR:
     inv[perm] = np.arange(g.n, dtype=np.uint32)
     src = np.repeat(np.arange(g.n, dtype=np.uint32), np.diff(g.row_off).astype(np.int64))
     return build_csr(g.n, inv[src], inv[g.col], g.w)
+
+
+def leb128(value: int) -> bytes:
+    """Unsigned LEB128: 7 bits per byte, least significant group first, the
+    high bit set on every byte but the last."""
+    out = bytearray()
+    while True:
+        b = value & 0x7F
+        value >>= 7
+        if value:
+            out.append(b | 0x80)
+        else:
+            out.append(b)
+            return bytes(out)
+
+
+def pack_gaps(col_off, row):
+    """Packed page columns of a CSC (not in the paper; a lossless form of its
+    compact pages): for each destination, its first source id and then each
+    gap to the next source minus one, every value as unsigned LEB128, the
+    destinations' bytes back to back.  Returns (boff[n+1] byte offsets, data)."""
+    col_off = np.asarray(col_off, dtype=np.int64)
+    row = np.asarray(row, dtype=np.int64)
+    n = col_off.shape[0] - 1
+    first = np.zeros(row.shape[0], dtype=bool)
+    first[col_off[:-1][np.diff(col_off) > 0]] = True
+    vals = row.copy()
+    gaps = np.zeros_like(row)
+    gaps[1:] = row[1:] - row[:-1] - 1
+    vals[~first] = gaps[~first]
+    nbytes = 1 + sum((vals >= (1 << (7 * k))).astype(np.int64) for k in range(1, 5))
+    pos = np.zeros(row.shape[0] + 1, dtype=np.int64)
+    np.cumsum(nbytes, out=pos[1:])
+    data = np.zeros(int(pos[-1]), dtype=np.uint8)
+    for k in range(5):
+        sel = nbytes > k
+        byte = (vals[sel] >> (7 * k)) & 0x7F
+        more = nbytes[sel] > k + 1
+        data[pos[:-1][sel] + k] = (byte | np.where(more, 0x80, 0)).astype(np.uint8)
+    boff = pos[col_off].astype(np.uint64)
+    return boff, data
+
+
+def unpack_gaps(boff, data, n: int):
+    """Inverse of pack_gaps (pure Python; small inputs): per destination the
+    list of source ids."""
+    out = []
+    for v in range(n):
+        ids, prev, val, shift = [], -1, 0, 0
+        for b in data[int(boff[v]):int(boff[v + 1])]:
+            val |= (int(b) & 0x7F) << shift
+            shift += 7
+            if not b & 0x80:
+                prev = val if not ids else prev + val + 1
+                ids.append(prev)
+                val, shift = 0, 0
+        out.append(ids)
+    return out
 
 
 def page_cut(n: int, col_off: np.ndarray, P: int) -> np.ndarray:

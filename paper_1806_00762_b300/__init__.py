@@ -52,8 +52,9 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
-def _flags(symmetrize: bool, reorder: bool) -> int:
-    return (C.SYMMETRIZE if symmetrize else 0) | (C.REORDER if reorder else 0)
+def _flags(symmetrize: bool, reorder: bool, compress: bool = False) -> int:
+    return ((C.SYMMETRIZE if symmetrize else 0) | (C.REORDER if reorder else 0) |
+            (C.COMPRESS if compress else 0))
 
 
 class Graph:
@@ -64,7 +65,7 @@ class Graph:
 
     @classmethod
     def from_edges(cls, n, src, dst, w=None, symmetrize=False, num_pages=1, stream=None,
-                   reorder=False):
+                   reorder=False, compress=False):
         ps, ms, ks = _ptr_mem(src)
         pd, md, kd = _ptr_mem(dst)
         pw, mw, kw = _ptr_mem(w)
@@ -77,18 +78,20 @@ class Graph:
             if arr is not None and not _is_u32(arr):
                 raise TypeError("edge arrays must hold 32-bit unsigned integers")
         out = ctypes.c_void_p()
-        C.check(C.lib().seraph_graph_from_edges(n, m, ps, pd, pw, ms, _flags(symmetrize, reorder),
+        C.check(C.lib().seraph_graph_from_edges(n, m, ps, pd, pw, ms,
+                                                _flags(symmetrize, reorder, compress),
                                                 num_pages, _stream_ptr(stream), ctypes.byref(out)))
         return cls(out.value)
 
     @classmethod
     def from_csr(cls, n, row_off, col, w=None, symmetrize=False, num_pages=1, stream=None,
-                 reorder=False):
+                 reorder=False, compress=False):
         pr, mr, kr = _ptr_mem(row_off)
         pc, mc, kc = _ptr_mem(col)
         pw, mw, kw = _ptr_mem(w)
         out = ctypes.c_void_p()
-        C.check(C.lib().seraph_graph_from_csr(n, pr, pc, pw, mr, _flags(symmetrize, reorder),
+        C.check(C.lib().seraph_graph_from_csr(n, pr, pc, pw, mr,
+                                              _flags(symmetrize, reorder, compress),
                                               num_pages, _stream_ptr(stream), ctypes.byref(out)))
         return cls(out.value)
 
@@ -113,6 +116,14 @@ class Graph:
                                                 None if w is None else w.ctypes.data,
                                                 od.ctypes.data))
         return col_off, row[:i["m"]], (None if w is None else w[:i["m"]]), od
+
+    def export_packed(self):
+        """(boff[n+1], data) of the packed gap streams (compress=True graphs)."""
+        i = self.info()
+        boff = np.empty(i["n"] + 1, dtype=np.uint64)
+        data = np.empty(max(i["packed_data_bytes"], 1), dtype=np.uint8)
+        C.check(C.lib().seraph_graph_export_packed(self._h, boff.ctypes.data, data.ctypes.data))
+        return boff, data[:i["packed_data_bytes"]]
 
     def perm(self) -> np.ndarray:
         """Internal vertex order: perm[i] = the caller's id of internal vertex i."""
@@ -248,6 +259,8 @@ def run(graph: Graph, algo, out=None, stream=None, **kw):
             v = C.PVUS[v]
         if k == "order" and isinstance(v, str):
             v = C.ORDERS[v]
+        if k == "columns" and isinstance(v, str):
+            v = C.COLUMNS[v]
         if k == "fsm_next":
             for i, x in enumerate(v):
                 p.fsm_next[i] = int(x)

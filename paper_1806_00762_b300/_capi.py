@@ -36,6 +36,8 @@ ORDER_CYCLIC, ORDER_ZIGZAG = 0, 1
 ORDERS = {"cyclic": ORDER_CYCLIC, "zigzag": ORDER_ZIGZAG}
 SYMMETRIZE = 1
 REORDER = 2
+COMPRESS = 4
+COLUMNS = {"auto": 0, "plain": 1, "packed": 2}
 NOALLOC_MAX_VERTICES = 1 << 20
 INF = 0xFFFFFFFF
 
@@ -48,7 +50,8 @@ class GraphInfo(ctypes.Structure):
                 ("weight_bytes", u64), ("max_page_struct_bytes", u64),
                 ("max_page_weight_bytes", u64), ("num_pages", u32), ("weighted", u32),
                 ("symmetrized", u32), ("max_in_degree", u32), ("weight_width", u32),
-                ("reordered", u32)]
+                ("reordered", u32), ("packed", u32), ("reserved", u32), ("packed_bytes", u64),
+                ("packed_data_bytes", u64), ("max_page_packed_bytes", u64)]
 
 
 class Params(ctypes.Structure):
@@ -60,7 +63,8 @@ class Params(ctypes.Structure):
                 ("sched", i32), ("timeout_ms", u32), ("profile", u32), ("order", u32),
                 ("max_passes", u32), ("slots", u32), ("group4_max_deg", u32),
                 ("group8_max_deg", u32),
-                ("sched_model", vp), ("stream", vp), ("trace", vp), ("l2_hot_bytes", u64)]
+                ("sched_model", vp), ("stream", vp), ("trace", vp), ("columns", u32),
+                ("pad1", u32), ("l2_hot_bytes", u64)]
 
 
 class Stats(ctypes.Structure):
@@ -109,6 +113,7 @@ PROTOTYPES = {
     "seraph_graph_page_bounds": (ctypes.c_int, [vp, vp]),
     "seraph_graph_export_csc": (ctypes.c_int, [vp, vp, vp, vp, vp]),
     "seraph_graph_export_perm": (ctypes.c_int, [vp, vp]),
+    "seraph_graph_export_packed": (ctypes.c_int, [vp, vp, vp]),
     "seraph_graph_free": (None, [vp]),
     "seraph_params_default": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int]),
     "seraph_run": (ctypes.c_int, [vp, ctypes.POINTER(Params), vp, ctypes.c_int,

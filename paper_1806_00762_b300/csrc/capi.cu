@@ -115,6 +115,14 @@ int seraph_graph_get_info(const seraph_graph* g, seraph_graph_info* info) {
         info->max_in_degree = g->max_in_degree;
         info->weight_width = g->weighted ? g->wbytes : 0;
         info->reordered = g->reordered;
+        info->packed = g->packed;
+        if (g->packed) {
+            info->packed_bytes = g->h_pack.bytes;
+            for (const auto& p : g->pages) {
+                info->packed_data_bytes += p.pk_data;
+                info->max_page_packed_bytes = std::max(info->max_page_packed_bytes, p.pk_bytes);
+            }
+        }
         return SERAPH_OK;
     });
 }
@@ -146,6 +154,24 @@ int seraph_graph_export_perm(const seraph_graph* g, uint32_t* perm) {
         } else {
             for (uint64_t i = 0; i < g->n; ++i) perm[i] = (uint32_t)i;
         }
+        return SERAPH_OK;
+    });
+}
+
+int seraph_graph_export_packed(const seraph_graph* g, uint64_t* boff, uint8_t* data) {
+    return guarded([&] {
+        SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
+        SR_CHECK(g->packed, SERAPH_EINVAL, "graph was built without SERAPH_COMPRESS");
+        uint64_t base = 0;
+        for (const auto& pm : g->pages) {
+            const uint8_t* h = g->h_pack.p + pm.pk_off;
+            const uint32_t* rel = (const uint32_t*)(h + pm.off_bytes);
+            if (boff)
+                for (uint64_t i = 0; i < pm.nv; ++i) boff[pm.vb + i] = base + rel[i];
+            if (data && pm.pk_data) std::memcpy(data + base, h + 2 * pm.off_bytes, pm.pk_data);
+            base += pm.pk_data;
+        }
+        if (boff) boff[g->n] = base;
         return SERAPH_OK;
     });
 }

@@ -271,7 +271,245 @@ __device__ __forceinline__ void gather8(const AlgoArgs& a, const PageLoc& loc, u
     }
 }
 
+// ----------------------------------------------------------- packed pages
+// A destination's sources are its first id, then each gap to the next id
+// minus one, as LEB128 codes (SERAPH_COMPRESS).  Lanes take aligned 16-byte
+// pieces of the code bytes and decode the codes that start in their piece:
+// a byte starts a code when the byte before it ends one (high bit clear).
+// The ids follow from a running sum, across pieces by a scan of the per-piece
+// (count, sum of value + 1) pairs.
+
+// Bit i (0..3) set: byte i of w ends a code.
+__device__ __forceinline__ uint32_t leb_ends4(uint32_t w) {
+    const uint32_t t = ~w & 0x80808080u;
+    return ((t >> 7) & 1u) | ((t >> 14) & 2u) | ((t >> 21) & 4u) | ((t >> 28) & 8u);
+}
+
+// Bits of the 16 bytes at c that start a code of the range [B, Eb); pt = the
+// byte before c ends a code (or c is the range's first piece).
+__device__ __forceinline__ uint32_t leb_starts(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                               uint32_t pt, uint32_t c, uint32_t B, uint32_t Eb) {
+    const uint32_t T = leb_ends4(w0) | (leb_ends4(w1) << 4) | (leb_ends4(w2) << 8) |
+                       (leb_ends4(w3) << 12);
+    const uint32_t lo = B > c ? B - c : 0u;                  // < 16
+    const uint32_t hi = Eb - c < 16u ? Eb - c : 16u;         // c < Eb
+    const uint32_t rng = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+    return ((T << 1) | pt) & rng;
+}
+
+template <int WB>
+__device__ __forceinline__ uint32_t ld_weight1(const uint8_t* w, uint32_t idx, uint64_t pol) {
+    uint32_t r;
+    if (WB == 1)
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(r) : "l"(w + idx), "l"(pol));
+    else if (WB == 2)
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=r"(r) : "l"(w + 2 * (uint64_t)idx), "l"(pol));
+    else
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(w + 4 * (uint64_t)idx), "l"(pol));
+    return r;
+}
+
+// One aligned 16-byte piece of a code range: the piece, the 4 bytes after it
+// (when still inside the range) and whether the byte before it ends a code.
+struct Piece {
+    uint32_t w0, w1, w2, w3, w4, pt;
+};
+
+// The 7-bit groups of 4 code bytes packed into 28 bits.
+__device__ __forceinline__ uint32_t leb_payload4(uint32_t w) {
+    return (w & 0x7Fu) | ((w >> 1) & 0x3F80u) | ((w >> 2) & 0x1FC000u) | ((w >> 3) & 0xFE00000u);
+}
+
+// Every code start of a piece decoded at once: the 7-bit groups of the 20
+// window bytes are packed into one bit stream (byte j's group at bit 7j), so
+// the code at byte j is the stream's bits [7j, 7j + 7L) with L = distance to
+// the first ending byte at or after j (the byte positions are compile-time
+// constants once unrolled).  lid[j] = sum of (value + 1) over the codes
+// starting at or before byte j, i.e. the id of the code at j relative to the
+// id before the piece.  Returns the piece's total.
+__device__ __forceinline__ uint32_t piece_decode(const Piece& P, uint32_t st, uint32_t lid[16]) {
+    const uint32_t p0 = leb_payload4(P.w0), p1 = leb_payload4(P.w1), p2 = leb_payload4(P.w2),
+                   p3 = leb_payload4(P.w3), p4 = leb_payload4(P.w4);
+    const uint32_t sw[6] = {p0 | (p1 << 28), (p1 >> 4) | (p2 << 24), (p2 >> 8) | (p3 << 20),
+                            (p3 >> 12) | (p4 << 16), p4 >> 16, 0u};
+    const uint32_t ends = leb_ends4(P.w0) | (leb_ends4(P.w1) << 4) | (leb_ends4(P.w2) << 8) |
+                          (leb_ends4(P.w3) << 12) | (leb_ends4(P.w4) << 16);
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int o = 7 * j, o5 = o + 28;
+        const uint32_t x = __funnelshift_r(sw[o >> 5], sw[(o >> 5) + 1], o & 31);
+        const uint32_t L = __ffs(ends >> j);  // code length 1..5 (0 only for a corrupt stream)
+        uint32_t v = x & ((1u << (7u * (L < 4u ? L : 4u))) - 1u);
+        if (L == 5u) v |= __funnelshift_r(sw[o5 >> 5], sw[(o5 >> 5) + 1], o5 & 31) << 28;
+        acc += ((st >> j) & 1u) ? v + 1u : 0u;
+        lid[j] = acc;
+    }
+    return acc;
+}
+
+// Gathers and reduction of a decoded piece, eight codes in flight at a time,
+// in code order: the code at byte j has id run + lid[j] (run = the id before
+// the piece; 0xFFFFFFFF before a destination's first) and edge index
+// e0 + ord + (codes before j in the piece).
 template <int ALGO, bool KAHAN, int WB>
+__device__ __forceinline__ void piece_gather(const AlgoArgs& a, const PageLoc& loc, uint32_t e0,
+                                             uint32_t st, const uint32_t lid[16], uint32_t run,
+                                             uint32_t ord, MinAcc& macc, SumAcc& sacc) {
+    const uint64_t pn = policy_evict_normal();
+    const uint64_t ps = a.hints ? policy_evict_first() : pn;
+    const uint64_t ph = a.hints ? policy_evict_last() : pn;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!((st >> (8 * h)) & 0xFFu)) continue;
+        uint32_t id[8], wt[8];
+        bool ok[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = 8 * h + k;
+            id[k] = run + lid[j];
+            ok[k] = ((st >> j) & 1u) && id[k] < a.n;  // a corrupt stream reads nothing
+            if (ALGO == ALG_SSSP)
+                wt[k] = ok[k] ? ld_weight1<WB>(loc.w, e0 + ord + __popc(st & ((1u << j) - 1u)), ps) : 0u;
+        }
+        if (ALGO == ALG_PR) {
+            float g[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                g[k] = ok[k] ? __uint_as_float(ld_gather(a.contrib + id[k], id[k] < a.hot ? ph : pn))
+                             : 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (ok[k]) sum_add<KAHAN>(sacc, g[k]);
+        } else {
+            uint32_t g[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                g[k] = ok[k] ? ld_gather(a.val + id[k], id[k] < a.hot ? ph : pn) : SERAPH_INF;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (!ok[k]) continue;
+                const uint32_t du = g[k];
+                if (ALGO == ALG_CC) {
+                    macc.best = min(macc.best, du);
+                } else if (du != SERAPH_INF) {
+                    const uint32_t s = du + (ALGO == ALG_SSSP ? wt[k] : 1u);
+                    if (s < du || s == SERAPH_INF) macc.ovf = true;
+                    else macc.best = min(macc.best, s);
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ Piece load_piece(const uint8_t* d, uint32_t c, uint32_t A, uint32_t Eb,
+                                            uint64_t pol) {
+    Piece P;
+    const uint4 q = ld_stream4(d + c, pol);
+    P.w0 = q.x; P.w1 = q.y; P.w2 = q.z; P.w3 = q.w;
+    P.w4 = c + 16u < Eb ? ld_stream(d + c + 16u, pol) : 0u;
+    P.pt = c == A ? 1u : ((ld_stream(d + c - 4u, pol) >> 31) ^ 1u);
+    return P;
+}
+
+// Thread per vertex: the pieces one after another, the running id carried.
+template <int ALGO, bool KAHAN, int WB>
+__device__ __forceinline__ void edges_packed_serial(const AlgoArgs& a, const PageLoc& loc,
+                                                    uint32_t li, uint32_t e0, MinAcc& macc,
+                                                    SumAcc& sacc) {
+    const uint8_t* d = (const uint8_t*)loc.col;
+    const uint32_t B = loc.boff[li], Eb = loc.boff[li + 1];
+    const uint64_t ps = a.hints ? policy_evict_first() : policy_evict_normal();
+    const uint32_t A = B & ~15u;
+    uint32_t run = 0xFFFFFFFFu, ord = 0;
+    for (uint32_t c = A; c < Eb; c += 16) {
+        const Piece P = load_piece(d, c, A, Eb, ps);
+        const uint32_t st = leb_starts(P.w0, P.w1, P.w2, P.w3, P.pt, c, B, Eb);
+        uint32_t lid[16];
+        const uint32_t sum = piece_decode(P, st, lid);
+        piece_gather<ALGO, KAHAN, WB>(a, loc, e0, st, lid, run, ord, macc, sacc);
+        run += sum;
+        ord += __popc(st);
+    }
+}
+
+// G lanes per vertex (G = 4, 8, 32; every lane of the warp calls this with a
+// warp-uniform trip count): lane t takes pieces t, t+G, ... and a width-G
+// scan of (count, sum) places its ids.
+template <int ALGO, bool KAHAN, int WB, int G>
+__device__ __forceinline__ void edges_packed_group(const AlgoArgs& a, const PageLoc& loc,
+                                                   bool valid, uint32_t li, uint32_t e0,
+                                                   uint32_t t, MinAcc& macc, SumAcc& sacc) {
+    const uint8_t* d = (const uint8_t*)loc.col;
+    uint32_t B = 0, Eb = 0;
+    if (valid) { B = loc.boff[li]; Eb = loc.boff[li + 1]; }
+    const uint64_t ps = a.hints ? policy_evict_first() : policy_evict_normal();
+    const uint32_t A = B & ~15u;
+    const uint32_t pieces = Eb > A ? (Eb - A + 15u) >> 4 : 0u;
+    const uint32_t iters = __reduce_max_sync(kFull, (pieces + G - 1) / G);
+    uint32_t run = 0xFFFFFFFFu, ord = 0;
+    for (uint32_t it = 0; it < iters; ++it) {
+        const uint32_t c = A + 16u * (it * G + t);
+        const bool act = valid && c < Eb;
+        Piece P{0u, 0u, 0u, 0u, 0u, 0u};
+        uint32_t st = 0;
+        if (act) {
+            P = load_piece(d, c, A, Eb, ps);
+            st = leb_starts(P.w0, P.w1, P.w2, P.w3, P.pt, c, B, Eb);
+        }
+        uint32_t lid[16];
+        const uint64_t x = ((uint64_t)__popc(st) << 32) | piece_decode(P, st, lid);
+        uint64_t inc = x;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(kFull, inc, o, G);
+            if (t >= (uint32_t)o) inc += y;
+        }
+        const uint64_t ex = inc - x;
+        const uint64_t tot = __shfl_sync(kFull, inc, G - 1, G);
+        if (st)
+            piece_gather<ALGO, KAHAN, WB>(a, loc, e0, st, lid, run + (uint32_t)ex,
+                                          ord + (uint32_t)(ex >> 32), macc, sacc);
+        run += (uint32_t)tot;
+        ord += (uint32_t)(tot >> 32);
+    }
+}
+
+// The whole CTA on one vertex: as above with a block-wide scan.
+template <int ALGO, bool KAHAN, int WB>
+__device__ __forceinline__ void edges_packed_cta(const AlgoArgs& a, const PageLoc& loc, uint32_t li,
+                                                 uint32_t e0, MinAcc& macc, SumAcc& sacc,
+                                                 unsigned long long* ws) {
+    const uint8_t* d = (const uint8_t*)loc.col;
+    const uint32_t B = loc.boff[li], Eb = loc.boff[li + 1];
+    const uint64_t ps = a.hints ? policy_evict_first() : policy_evict_normal();
+    const uint32_t A = B & ~15u;
+    const uint32_t pieces = Eb > A ? (Eb - A + 15u) >> 4 : 0u;
+    const uint32_t iters = (pieces + kNT - 1) / kNT;
+    uint32_t run = 0xFFFFFFFFu, ord = 0;
+    for (uint32_t it = 0; it < iters; ++it) {
+        const uint32_t c = A + 16u * (it * kNT + threadIdx.x);
+        const bool act = c < Eb;
+        Piece P{0u, 0u, 0u, 0u, 0u, 0u};
+        uint32_t st = 0;
+        if (act) {
+            P = load_piece(d, c, A, Eb, ps);
+            st = leb_starts(P.w0, P.w1, P.w2, P.w3, P.pt, c, B, Eb);
+        }
+        uint32_t lid[16];
+        const unsigned long long x =
+            ((unsigned long long)__popc(st) << 32) | piece_decode(P, st, lid);
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan<kNT>(x, ws, &tot);
+        if (st)
+            piece_gather<ALGO, KAHAN, WB>(a, loc, e0, st, lid, run + (uint32_t)ex,
+                                          ord + (uint32_t)(ex >> 32), macc, sacc);
+        run += (uint32_t)tot;
+        ord += (uint32_t)(tot >> 32);
+    }
+}
+
+template <int ALGO, bool KAHAN, int WB, bool PK>
 __device__ __forceinline__ void vertex_thread(const AlgoArgs& a, unsigned long long ent, float base,
                                               Locals& L) {
     const uint32_t v = (uint32_t)ent, p = (uint32_t)(ent >> 32);
@@ -281,8 +519,12 @@ __device__ __forceinline__ void vertex_thread(const AlgoArgs& a, unsigned long l
     const uint32_t b = loc.off[li], e = loc.off[li + 1];
     MinAcc macc{SERAPH_INF, false};
     SumAcc sacc{0.f, 0.f};
-    for (uint32_t idx = b & ~3u; idx < e; idx += 8)
-        gather8<ALGO, KAHAN, WB>(a, loc, b, e, idx, idx + 4, macc, sacc);
+    if constexpr (PK) {
+        edges_packed_serial<ALGO, KAHAN, WB>(a, loc, li, b, macc, sacc);
+    } else {
+        for (uint32_t idx = b & ~3u; idx < e; idx += 8)
+            gather8<ALGO, KAHAN, WB>(a, loc, b, e, idx, idx + 4, macc, sacc);
+    }
     if (ALGO == ALG_PR) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L, own);
     else finish_min<ALGO>(a, v, macc, e - b, L, own);
 }
@@ -303,7 +545,7 @@ __device__ __forceinline__ void edges_strided(const AlgoArgs& a, const PageLoc& 
 // offsets, columns, gathered values) overlap.  Every lane of the warp calls
 // this (inactive groups pass valid = false) because the group reduction
 // shuffles across the whole warp; xor offsets below G stay inside a group.
-template <int ALGO, bool KAHAN, int WB, int G>
+template <int ALGO, bool KAHAN, int WB, int G, bool PK>
 __device__ __forceinline__ void vertex_group(const AlgoArgs& a, unsigned long long ent, bool valid,
                                              float base, Locals& L) {
     const uint32_t t = lane_id() & (G - 1);
@@ -311,7 +553,19 @@ __device__ __forceinline__ void vertex_group(const AlgoArgs& a, unsigned long lo
     SumAcc sacc{0.f, 0.f};
     uint32_t v = 0, b = 0, e = 0;
     Own own{0u, 0.f, 0};
-    if (valid) {
+    if constexpr (PK) {
+        PageLoc loc{};
+        uint32_t li = 0;
+        if (valid) {
+            v = (uint32_t)ent;
+            if (t == 0) own = load_own<ALGO>(a, v);
+            loc = a.loc[(uint32_t)(ent >> 32)];
+            li = v - loc.vb;
+            b = loc.off[li];
+            e = loc.off[li + 1];
+        }
+        edges_packed_group<ALGO, KAHAN, WB, G>(a, loc, valid, li, b, t, macc, sacc);
+    } else if (valid) {
         v = (uint32_t)ent;
         if (t == 0) own = load_own<ALGO>(a, v);
         const PageLoc loc = a.loc[(uint32_t)(ent >> 32)];
@@ -337,10 +591,11 @@ __device__ __forceinline__ void vertex_group(const AlgoArgs& a, unsigned long lo
     }
 }
 
-template <int ALGO, bool KAHAN, int WB>
+template <int ALGO, bool KAHAN, int WB, bool PK>
 __device__ __forceinline__ void vertex_cta(const AlgoArgs& a, unsigned long long ent, float base,
                                            Locals& L, float* s_sum, float* s_comp,
-                                           unsigned* s_min, unsigned* s_ovf) {
+                                           unsigned* s_min, unsigned* s_ovf,
+                                           unsigned long long* s_scan) {
     const uint32_t v = (uint32_t)ent, p = (uint32_t)(ent >> 32);
     const PageLoc loc = a.loc[p];
     const uint32_t li = v - loc.vb;
@@ -350,7 +605,8 @@ __device__ __forceinline__ void vertex_cta(const AlgoArgs& a, unsigned long long
     if (threadIdx.x == 0) own = load_own<ALGO>(a, v);
     MinAcc macc{SERAPH_INF, false};
     SumAcc sacc{0.f, 0.f};
-    edges_strided<ALGO, KAHAN, WB>(a, loc, b, e, threadIdx.x, kNT, macc, sacc);
+    if constexpr (PK) edges_packed_cta<ALGO, KAHAN, WB>(a, loc, li, b, macc, sacc, s_scan);
+    else edges_strided<ALGO, KAHAN, WB>(a, loc, b, e, threadIdx.x, kNT, macc, sacc);
     if (ALGO == ALG_PR) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -496,7 +752,7 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
 
 // Class-k list (k = 1, 2, 3) with G lanes per vertex: each warp grabs
 // 4 * 32/G entries at a time.
-template <int ALGO, bool KAHAN, int WB, int G>
+template <int ALGO, bool KAHAN, int WB, int G, bool PK>
 __device__ __forceinline__ void group_phase(const AlgoArgs& a, int par, int k, float base,
                                             Locals& L) {
     constexpr unsigned per = 32 / G;
@@ -511,7 +767,7 @@ __device__ __forceinline__ void group_phase(const AlgoArgs& a, int par, int k, f
         for (unsigned r = 0; r < 4; ++r) {
             const unsigned i = i0 + r * per + grp;
             const bool valid = i < n;
-            vertex_group<ALGO, KAHAN, WB, G>(a, valid ? a.list[k][i] : 0ull, valid, base, L);
+            vertex_group<ALGO, KAHAN, WB, G, PK>(a, valid ? a.list[k][i] : 0ull, valid, base, L);
         }
     }
 }
@@ -519,10 +775,11 @@ __device__ __forceinline__ void group_phase(const AlgoArgs& a, int par, int k, f
 // Six CTAs per SM (<= 42 registers) keep enough warps in flight for the
 // gathers (PageRank's compensated sums would otherwise take 48); SSSP's
 // weights need more registers, five CTAs (<= 51).
-template <int ALGO, bool KAHAN, int WB>
-__global__ void __launch_bounds__(kNT, ALGO == ALG_SSSP ? 5 : 6)
+template <int ALGO, bool KAHAN, int WB, bool PK>
+__global__ void __launch_bounds__(kNT, PK ? 4 : (ALGO == ALG_SSSP ? 5 : 6))
     relax_kernel(AlgoArgs a, uint32_t pass, uint32_t step) {
     __shared__ unsigned s_item;
+    __shared__ unsigned long long s_scan[kNT / 32 + 1];
     __shared__ float s_sum[kNT / 32], s_comp[kNT / 32];
     __shared__ unsigned s_min[kNT / 32], s_ovf[kNT / 32];
     const int par = pass & 1;
@@ -539,11 +796,12 @@ __global__ void __launch_bounds__(kNT, ALGO == ALG_SSSP ? 5 : 6)
         const unsigned i = s_item;
         __syncthreads();
         if (i >= n_cta) break;
-        vertex_cta<ALGO, KAHAN, WB>(a, a.list[4][i], base, L, s_sum, s_comp, s_min, s_ovf);
+        vertex_cta<ALGO, KAHAN, WB, PK>(a, a.list[4][i], base, L, s_sum, s_comp, s_min, s_ovf,
+                                        s_scan);
     }
-    group_phase<ALGO, KAHAN, WB, 32>(a, par, 3, base, L);
-    group_phase<ALGO, KAHAN, WB, 8>(a, par, 2, base, L);
-    group_phase<ALGO, KAHAN, WB, 4>(a, par, 1, base, L);
+    group_phase<ALGO, KAHAN, WB, 32, PK>(a, par, 3, base, L);
+    group_phase<ALGO, KAHAN, WB, 8, PK>(a, par, 2, base, L);
+    group_phase<ALGO, KAHAN, WB, 4, PK>(a, par, 1, base, L);
     const unsigned lane = lane_id();
     const unsigned n0 = rs->list_cnt[par][0];
     for (;;) {  // one thread per small vertex, 128 per warp grab
@@ -554,7 +812,7 @@ __global__ void __launch_bounds__(kNT, ALGO == ALG_SSSP ? 5 : 6)
 #pragma unroll
         for (unsigned j = 0; j < 4; ++j) {
             const unsigned i = i0 + j * 32 + lane;
-            if (i < n0) vertex_thread<ALGO, KAHAN, WB>(a, a.list[0][i], base, L);
+            if (i < n0) vertex_thread<ALGO, KAHAN, WB, PK>(a, a.list[0][i], base, L);
         }
     }
     flush_locals(a, par, step, L);
@@ -579,14 +837,15 @@ __global__ void __launch_bounds__(kNT) pr_apply_kernel(AlgoArgs a, uint32_t pass
 __global__ void set_locs_kernel(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t end,
                                 const uint64_t* rel_soff, const uint64_t* rel_woff,
                                 const uint64_t* off_bytes, uint8_t* sbase, uint8_t* wbase,
-                                RunState* rs, uint32_t seq) {
+                                bool packed, RunState* rs, uint32_t seq) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile unsigned*)&rs->loaded = seq;
     for (uint32_t p = first + blockIdx.x * blockDim.x + threadIdx.x; p < end;
          p += gridDim.x * blockDim.x) {
         PageLoc L;
         const uint8_t* s = sbase + rel_soff[p];
         L.off = (const uint32_t*)s;
-        L.col = (const uint32_t*)(s + off_bytes[p]);
+        L.boff = packed ? (const uint32_t*)(s + off_bytes[p]) : nullptr;
+        L.col = (const uint32_t*)(s + (packed ? 2 : 1) * off_bytes[p]);
         L.w = wbase ? wbase + rel_woff[p] : nullptr;
         L.vb = vb[p];
         L.nv = vb[p + 1] - vb[p];
@@ -739,21 +998,28 @@ void launch_compact(int algo, const WindowDesc& wd, const AlgoArgs& a, uint32_t 
     SR_LAUNCH();
 }
 
-void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, uint32_t step, int grid,
-                  cudaStream_t s) {
+template <bool PK>
+void launch_relax_form(int algo, int kahan, const AlgoArgs& a, uint32_t pass, uint32_t step,
+                       int grid, cudaStream_t s) {
     switch (algo) {
         case ALG_SSSP:
-            if (a.wbytes == 1) relax_kernel<ALG_SSSP, false, 1><<<grid, kNT, 0, s>>>(a, pass, step);
-            else if (a.wbytes == 2) relax_kernel<ALG_SSSP, false, 2><<<grid, kNT, 0, s>>>(a, pass, step);
-            else relax_kernel<ALG_SSSP, false, 4><<<grid, kNT, 0, s>>>(a, pass, step);
+            if (a.wbytes == 1) relax_kernel<ALG_SSSP, false, 1, PK><<<grid, kNT, 0, s>>>(a, pass, step);
+            else if (a.wbytes == 2) relax_kernel<ALG_SSSP, false, 2, PK><<<grid, kNT, 0, s>>>(a, pass, step);
+            else relax_kernel<ALG_SSSP, false, 4, PK><<<grid, kNT, 0, s>>>(a, pass, step);
             break;
-        case ALG_BFS: relax_kernel<ALG_BFS, false, 4><<<grid, kNT, 0, s>>>(a, pass, step); break;
-        case ALG_CC: relax_kernel<ALG_CC, false, 4><<<grid, kNT, 0, s>>>(a, pass, step); break;
+        case ALG_BFS: relax_kernel<ALG_BFS, false, 4, PK><<<grid, kNT, 0, s>>>(a, pass, step); break;
+        case ALG_CC: relax_kernel<ALG_CC, false, 4, PK><<<grid, kNT, 0, s>>>(a, pass, step); break;
         default:
-            if (kahan) relax_kernel<ALG_PR, true, 4><<<grid, kNT, 0, s>>>(a, pass, step);
-            else relax_kernel<ALG_PR, false, 4><<<grid, kNT, 0, s>>>(a, pass, step);
+            if (kahan) relax_kernel<ALG_PR, true, 4, PK><<<grid, kNT, 0, s>>>(a, pass, step);
+            else relax_kernel<ALG_PR, false, 4, PK><<<grid, kNT, 0, s>>>(a, pass, step);
             break;
     }
+}
+
+void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, uint32_t step, int grid,
+                  cudaStream_t s) {
+    if (a.packed) launch_relax_form<true>(algo, kahan, a, pass, step, grid, s);
+    else launch_relax_form<false>(algo, kahan, a, pass, step, grid, s);
     SR_LAUNCH();
 }
 
@@ -764,10 +1030,11 @@ void launch_pr_apply(const AlgoArgs& a, uint32_t pass, int grid, cudaStream_t s)
 
 void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t end,
                      const uint64_t* rel_soff, const uint64_t* rel_woff, const uint64_t* off_bytes,
-                     uint8_t* sbase, uint8_t* wbase, RunState* rs, uint32_t seq, cudaStream_t s) {
+                     uint8_t* sbase, uint8_t* wbase, bool packed, RunState* rs, uint32_t seq,
+                     cudaStream_t s) {
     unsigned g = end > first ? (end - first + kNT - 1) / kNT : 1;
     set_locs_kernel<<<g, kNT, 0, s>>>(loc, vb, first, end, rel_soff, rel_woff, off_bytes, sbase,
-                                       wbase, rs, seq);
+                                       wbase, packed, rs, seq);
     SR_LAUNCH();
 }
 

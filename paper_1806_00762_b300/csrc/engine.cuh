@@ -16,8 +16,9 @@ constexpr int kClasses = 5;
 // edge ring).  Rewritten whenever the page's chunk is (re)loaded.
 struct PageLoc {
     const uint32_t* off;  // nv+1 page-relative offsets
-    const uint32_t* col;  // ne source ids (16-byte aligned)
+    const uint32_t* col;  // ne source ids (16-byte aligned); packed: the gap stream
     const uint8_t* w;     // ne weights, wbytes each (16-byte aligned) or null
+    const uint32_t* boff; // packed: nv+1 byte offsets into the gap stream, else null
     uint32_t vb;          // first vertex
     uint32_t nv;          // vertices
 };
@@ -88,7 +89,9 @@ struct AlgoArgs {
     uint8_t pvu;              // SERAPH_PVU_*
     uint8_t wbytes;           // stored weight width: 1, 2 or 4 bytes
     uint8_t hints;            // 1: L2 eviction-priority hints on (see hot)
+    uint8_t packed;           // pages hold LEB128 gap streams (SERAPH_COMPRESS)
     uint32_t hot;             // gathers of vertices < hot: L2 evict-last
+    uint32_t n;               // vertices
 };
 
 // Launchers (engine.cu).  `pass` is the global pass counter (its parity picks
@@ -110,7 +113,8 @@ void launch_relax(int algo, int kahan, const AlgoArgs& a, uint32_t pass, uint32_
 void launch_pr_apply(const AlgoArgs& a, uint32_t pass, int grid, cudaStream_t s);
 void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t end,
                      const uint64_t* rel_soff, const uint64_t* rel_woff, const uint64_t* off_bytes,
-                     uint8_t* sbase, uint8_t* wbase, RunState* rs, uint32_t seq, cudaStream_t s);
+                     uint8_t* sbase, uint8_t* wbase, bool packed, RunState* rs, uint32_t seq,
+                     cudaStream_t s);
 void launch_init_values(int algo, const AlgoArgs& a, uint64_t n, uint32_t source,
                         const uint32_t* label0, cudaStream_t s);
 // out[v] = in[inv[v]]: values of a reordered graph back in the caller's ids.

@@ -22,6 +22,15 @@ struct PageMeta {
     uint64_t w_off;     // byte offset in the weight region
     uint64_t w_bytes;   // weight bytes (ne * weight width, padded), 0 if unweighted
     uint32_t maxdeg;    // largest in-degree in the page
+    // Packed structure (SERAPH_COMPRESS), in its own region:
+    //   u32 off[nv+1] as above, padded to 16 B,
+    //   u32 boff[nv+1] byte offsets into the page's gap stream, padded to 16 B,
+    //   the gap stream: per destination, its first source id and then each
+    //   gap to the next source minus one, LEB128 (7 bits per byte, low group
+    //   first, high bit set on every byte but a value's last), padded to 16 B.
+    uint64_t pk_off;    // byte offset of the page in the packed region
+    uint64_t pk_bytes;  // packed structure bytes (padded)
+    uint64_t pk_data;   // gap-stream bytes (unpadded)
 };
 
 struct seraph_graph {
@@ -38,6 +47,9 @@ struct seraph_graph {
     seraph::DevBuf<uint32_t> d_outdeg; // out-degree per vertex (PageRank)
     seraph::DevBuf<uint32_t> d_vb;     // page boundaries (u32) on the device
     seraph::DevBuf<uint32_t> d_zero_in; // bit v set: v has no in-edge
+    bool packed = false;               // built with SERAPH_COMPRESS
+    seraph::PinnedBuf h_pack;          // all packed page structures, in page order
+    seraph::DevBuf<uint8_t> d_pack_tmp; // gap streams while the graph is built
     bool reordered = false;            // built with SERAPH_REORDER
     seraph::DevBuf<uint32_t> d_perm;   // internal id -> caller's id (reordered only)
     seraph::DevBuf<uint32_t> d_inv;    // caller's id -> internal id (reordered only)

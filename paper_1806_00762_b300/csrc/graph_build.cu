@@ -468,6 +468,65 @@ __global__ void split_keys_kernel(const uint64_t* __restrict__ keys, uint64_t E,
     }
 }
 
+// ------------------------------------------------------- packed columns
+
+__device__ __forceinline__ uint32_t leb_len(uint32_t v) {
+    return v < (1u << 7) ? 1u : v < (1u << 14) ? 2u : v < (1u << 21) ? 3u : v < (1u << 28) ? 4u : 5u;
+}
+
+// Bit e set: edge e is the first in-edge of its destination.
+__global__ void first_bits_kernel(const uint64_t* __restrict__ col_off, uint64_t n,
+                                  uint32_t* __restrict__ bits) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = col_off[v];
+        if (e < col_off[v + 1]) atomicOr(&bits[e >> 5], 1u << (e & 31));
+    }
+}
+
+// The value stored for edge e: its source id if it is its destination's
+// first in-edge, else the gap to the previous source minus one (sources are
+// strictly ascending within a destination).
+__device__ __forceinline__ uint32_t gap_value(const uint32_t* __restrict__ col,
+                                              const uint32_t* __restrict__ first, uint64_t e) {
+    const bool f = (first[e >> 5] >> (e & 31)) & 1u;
+    return f ? col[e] : col[e] - col[e - 1] - 1u;
+}
+
+__global__ void leb_len_kernel(const uint32_t* __restrict__ col, const uint32_t* __restrict__ first,
+                               uint64_t E, uint8_t* __restrict__ lens) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E;
+         e += (uint64_t)gridDim.x * blockDim.x)
+        lens[e] = (uint8_t)leb_len(gap_value(col, first, e));
+}
+
+__global__ void leb_write_kernel(const uint32_t* __restrict__ col, const uint32_t* __restrict__ first,
+                                 uint64_t E, const uint64_t* __restrict__ pos,
+                                 uint8_t* __restrict__ data) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v = gap_value(col, first, e);
+        uint64_t q = pos[e];
+        for (;;) {
+            const uint8_t b = (uint8_t)(v & 0x7Fu);
+            v >>= 7;
+            if (!v) { data[q] = b; break; }
+            data[q++] = b | 0x80u;
+        }
+    }
+}
+
+// Global byte offset of each destination's bytes (n+1 entries).
+__global__ void vertex_boff_kernel(const uint64_t* __restrict__ col_off, uint64_t n,
+                                   const uint64_t* __restrict__ pos, uint64_t E, uint64_t total,
+                                   uint64_t* __restrict__ gboff) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v <= n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = col_off[v];
+        gboff[v] = e < E ? pos[e] : total;
+    }
+}
+
 int bits_for(uint64_t n) {
     int b = 1;
     while (b < 64 && (1ull << b) < n) ++b;
@@ -635,6 +694,82 @@ void sorted_adjacency(uint64_t n, uint64_t m, const uint32_t* lo_in, const uint3
     SR_CUDA(cudaStreamSynchronize(s));
 }
 
+// The packed page form (SERAPH_COMPRESS): LEB128 gap streams of every
+// destination's sources, encoded on the device, then laid out per page in
+// pinned memory as off (copied from `stage`), boff and the stream bytes.
+void build_packed(seraph_graph* g, uint64_t n, uint64_t E, const uint32_t* col,
+                  const uint64_t* col_off, const uint64_t* d_vb, const uint64_t* d_st,
+                  const std::vector<uint64_t>& st, const DevBuf<uint32_t>& stage, cudaStream_t s) {
+    const uint32_t P = g->num_pages;
+    DevBuf<uint64_t> pos(std::max<uint64_t>(E, 1));
+    uint64_t total = 0;
+    if (E) {
+        DevBuf<uint32_t> first((E + 31) / 32);
+        SR_CUDA(cudaMemsetAsync(first.p, 0, ((E + 31) / 32) * sizeof(uint32_t), s));
+        first_bits_kernel<<<grid_for(n), kNT, 0, s>>>(col_off, n, first.p);
+        SR_LAUNCH();
+        {
+            DevBuf<uint8_t> lens(E);
+            leb_len_kernel<<<grid_for(E), kNT, 0, s>>>(col, first.p, E, lens.p);
+            SR_LAUNCH();
+            exclusive_scan<uint8_t>(lens.p, E, pos.p, s);
+            uint64_t last_pos = 0;
+            uint8_t last_len = 0;
+            SR_CUDA(cudaMemcpyAsync(&last_pos, pos.p + E - 1, 8, cudaMemcpyDeviceToHost, s));
+            SR_CUDA(cudaMemcpyAsync(&last_len, lens.p + E - 1, 1, cudaMemcpyDeviceToHost, s));
+            SR_CUDA(cudaStreamSynchronize(s));
+            total = last_pos + last_len;
+        }
+        DevBuf<uint8_t> data(total);
+        leb_write_kernel<<<grid_for(E), kNT, 0, s>>>(col, first.p, E, pos.p, data.p);
+        SR_LAUNCH();
+        SR_CUDA(cudaStreamSynchronize(s));
+        g->d_pack_tmp = std::move(data);
+    }
+    DevBuf<uint64_t> gboff(n + 1);
+    vertex_boff_kernel<<<grid_for(n + 1), kNT, 0, s>>>(col_off, n, pos.p, E, total, gboff.p);
+    SR_LAUNCH();
+    SR_CUDA(cudaStreamSynchronize(s));
+    pos.release();
+    DevBuf<uint64_t> d_gb(P + 1);
+    gather_off_kernel<<<grid_for(P + 1), kNT, 0, s>>>(gboff.p, d_vb, P, d_gb.p);
+    SR_LAUNCH();
+    std::vector<uint64_t> gb(P + 1);
+    SR_CUDA(cudaMemcpyAsync(gb.data(), d_gb.p, (P + 1) * 8, cudaMemcpyDeviceToHost, s));
+    DevBuf<uint32_t> bstage(st[P]);
+    DevBuf<unsigned> pmax(P);
+    SR_CUDA(cudaMemsetAsync(pmax.p, 0, P * sizeof(unsigned), s));
+    stage_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(gboff.p, d_vb, d_st, P, n, bstage.p, pmax.p);
+    SR_LAUNCH();
+    SR_CUDA(cudaStreamSynchronize(s));
+    uint64_t pk_off = 0;
+    for (uint32_t p = 0; p < P; ++p) {
+        PageMeta& pm = g->pages[p];
+        pm.pk_data = gb[p + 1] - gb[p];
+        SR_CHECK(pm.pk_data < 0xFFFFFFFFull, SERAPH_EOVERFLOW, "a packed page holds 2^32 or more bytes");
+        pm.pk_off = pk_off;
+        pm.pk_bytes = 2 * pm.off_bytes + align_up(pm.pk_data, 16);
+        pk_off += pm.pk_bytes;
+    }
+    g->h_pack.alloc(pk_off);
+    for (uint32_t p = 0; p < P; ++p) {
+        const PageMeta& pm = g->pages[p];
+        uint8_t* h = g->h_pack.p + pm.pk_off;
+        const uint64_t ob = 4 * (pm.nv + 1);
+        SR_CUDA(cudaMemcpyAsync(h, stage.p + st[p], ob, cudaMemcpyDeviceToHost, s));
+        std::memset(h + ob, 0, pm.off_bytes - ob);
+        SR_CUDA(cudaMemcpyAsync(h + pm.off_bytes, bstage.p + st[p], ob, cudaMemcpyDeviceToHost, s));
+        std::memset(h + pm.off_bytes + ob, 0, pm.off_bytes - ob);
+        uint8_t* hd = h + 2 * pm.off_bytes;
+        if (pm.pk_data)
+            SR_CUDA(cudaMemcpyAsync(hd, g->d_pack_tmp.p + gb[p], pm.pk_data, cudaMemcpyDeviceToHost, s));
+        std::memset(hd + pm.pk_data, 0, align_up(pm.pk_data, 16) - pm.pk_data);
+    }
+    SR_CUDA(cudaStreamSynchronize(s));
+    g->d_pack_tmp.release();
+    g->packed = true;
+}
+
 void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in,
                  const uint32_t* dst_in, const uint32_t* w_in, int mem, uint32_t flags,
                  uint32_t P, cudaStream_t s) {
@@ -643,7 +778,8 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     SR_CHECK(mem == SERAPH_MEM_HOST || mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad mem kind");
     SR_CHECK(m == 0 || (src_in && dst_in), SERAPH_EINVAL, "src/dst must not be NULL");
     SR_CHECK(m < (1ull << 36), SERAPH_EINVAL, "too many edges");
-    SR_CHECK((flags & ~(SERAPH_SYMMETRIZE | SERAPH_REORDER)) == 0, SERAPH_EINVAL, "unknown flag");
+    SR_CHECK((flags & ~(SERAPH_SYMMETRIZE | SERAPH_REORDER | SERAPH_COMPRESS)) == 0, SERAPH_EINVAL,
+             "unknown flag");
     const bool sym = flags & SERAPH_SYMMETRIZE;
     const bool reorder = flags & SERAPH_REORDER;
     const bool weighted = w_in != nullptr;
@@ -756,6 +892,7 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
         }
     }
     SR_CUDA(cudaStreamSynchronize(s));
+    if (flags & SERAPH_COMPRESS) build_packed(g, n, E, col.p, col_off.p, d_vb.p, d_st.p, st, stage, s);
 }
 
 void build_graph_csr(seraph_graph* g, uint64_t n, const uint64_t* row_off_in, const uint32_t* col_in,

@@ -207,6 +207,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CUDA(cudaSetDevice(g->device));
 
     // ------------------------------------------------------------ chunking
+    SR_CHECK(P->columns <= SERAPH_COLUMNS_PACKED, SERAPH_EINVAL, "bad columns");
+    const bool packed = P->columns == SERAPH_COLUMNS_PACKED ||
+                        (P->columns == SERAPH_COLUMNS_AUTO && g->packed);
+    SR_CHECK(!packed || g->packed, SERAPH_EINVAL, "graph was built without SERAPH_COMPRESS");
+    // structure bytes of a page in the streamed form (plain u32 columns or packed gaps)
+    auto st_off = [&](const PageMeta& pm) { return packed ? pm.pk_off : pm.s_off; };
+    auto st_bytes = [&](const PageMeta& pm) { return packed ? pm.pk_bytes : pm.s_bytes; };
+    const uint8_t* h_struct = packed ? g->h_pack.p : g->h_struct.p;
     const uint32_t W = P->window;
     const uint32_t R = P->slots ? P->slots : W + 1;
     SR_CHECK(R >= W + 1 && R <= 4096, SERAPH_EINVAL, "slots must be in [window+1, 4096]");
@@ -219,18 +227,18 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         for (uint32_t p = 0; p < g->num_pages; ++p) {
             const PageMeta& pm = g->pages[p];
             const uint64_t wb = use_w ? pm.w_bytes : 0;
-            SR_CHECK(align_up(pm.s_bytes, 256) + wb <= slot_bytes, SERAPH_EBUDGET,
-                     "page " + std::to_string(p) + " (" + std::to_string(pm.s_bytes + wb) +
+            SR_CHECK(align_up(st_bytes(pm), 256) + wb <= slot_bytes, SERAPH_EBUDGET,
+                     "page " + std::to_string(p) + " (" + std::to_string(st_bytes(pm) + wb) +
                          " B) does not fit a ring slot of " + std::to_string(slot_bytes) + " B");
-            if (open && align_up(cur.s_bytes + pm.s_bytes, 256) + cur.w_bytes + wb <= slot_bytes) {
+            if (open && align_up(cur.s_bytes + st_bytes(pm), 256) + cur.w_bytes + wb <= slot_bytes) {
                 cur.end_page = p + 1;
-                cur.s_bytes += pm.s_bytes;
+                cur.s_bytes += st_bytes(pm);
                 cur.w_bytes += wb;
                 cur.v_end = (uint32_t)(pm.vb + pm.nv);
                 continue;
             }
             if (open) chunks.push_back(cur);
-            cur = Chunk{p, p + 1, pm.s_off, pm.s_bytes, pm.w_off, wb, 0, (uint32_t)pm.vb,
+            cur = Chunk{p, p + 1, st_off(pm), st_bytes(pm), pm.w_off, wb, 0, (uint32_t)pm.vb,
                         (uint32_t)(pm.vb + pm.nv)};
             open = true;
         }
@@ -245,7 +253,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     std::vector<uint64_t> rel_soff(g->num_pages), rel_woff(g->num_pages), offb(g->num_pages);
     for (const Chunk& c : chunks)
         for (uint32_t p = c.first_page; p < c.end_page; ++p) {
-            rel_soff[p] = g->pages[p].s_off - c.s_begin;
+            rel_soff[p] = st_off(g->pages[p]) - c.s_begin;
             rel_woff[p] = c.w_slot_off + (g->pages[p].w_off - c.w_begin);
             offb[p] = g->pages[p].off_bytes;
         }
@@ -317,6 +325,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     a.skip_mask = P->fsm_skip_mask;
     a.pvu = (uint8_t)P->pvu;
     a.wbytes = (uint8_t)g->wbytes;
+    a.packed = packed;
+    a.n = (uint32_t)n;
     {
         uint64_t hot_bytes = P->l2_hot_bytes;
         if (hot_bytes == SERAPH_L2_HOT_AUTO) {
@@ -463,13 +473,13 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         const Chunk& ch = chunks[c];
         uint8_t* sb = ebuf.p + (uint64_t)slot * slot_bytes;
         if (prof) SR_CUDA(cudaEventRecord(pc_b[(load_seq + 1) % ring].e, xs.s));
-        SR_CUDA(cudaMemcpyAsync(sb, g->h_struct.p + ch.s_begin, ch.s_bytes, cudaMemcpyHostToDevice, xs.s));
+        SR_CUDA(cudaMemcpyAsync(sb, h_struct + ch.s_begin, ch.s_bytes, cudaMemcpyHostToDevice, xs.s));
         if (use_w && ch.w_bytes)
             SR_CUDA(cudaMemcpyAsync(sb + ch.w_slot_off, g->h_weight.p + ch.w_begin, ch.w_bytes,
                                     cudaMemcpyHostToDevice, xs.s));
         if (prof) SR_CUDA(cudaEventRecord(pc_e[(load_seq + 1) % ring].e, xs.s));
         launch_set_locs(loc.p, g->d_vb.p, ch.first_page, ch.end_page, d_rel_soff.p, d_rel_woff.p,
-                        d_offb.p, sb, use_w ? sb : nullptr, rs.p, ++load_seq, xs.s);
+                        d_offb.p, sb, use_w ? sb : nullptr, packed, rs.p, ++load_seq, xs.s);
         ++launches;
         SR_CUDA(cudaEventRecord(copy_done[c].e, xs.s));
         slot_of[c] = slot;

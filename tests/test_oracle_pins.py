@@ -158,6 +158,37 @@ def test_degree_order_by_brute_force_and_relabel_is_an_isomorphism():
         assert np.all(np.diff(h.out_degree().astype(np.int64)) <= 0)
 
 
+def test_leb128_published_example_and_boundaries():
+    """The unsigned-LEB128 example of the DWARF specification (624485 ->
+    E5 8E 26) and the code-length boundaries of the definition."""
+    assert oracle.leb128(624485) == bytes([0xE5, 0x8E, 0x26])
+    assert oracle.leb128(0) == b"\x00" and oracle.leb128(127) == b"\x7f"
+    assert oracle.leb128(128) == b"\x80\x01" and oracle.leb128(16383) == b"\xff\x7f"
+    assert oracle.leb128(16384) == b"\x80\x80\x01"
+    assert oracle.leb128(2**32 - 1) == b"\xff\xff\xff\xff\x0f"
+
+
+def test_pack_gaps_against_scalar_codes_and_decoder():
+    rng = np.random.default_rng(3)
+    for seed in range(5):
+        n = 60
+        src, dst, _ = graphs.random_graph(n, 400, seed=seed)
+        g = oracle.build_csr(n, src, dst)
+        col_off, row, _ = oracle.csc(g)
+        # scale ids up so that 1- to 5-byte codes all occur
+        big = (row.astype(np.int64) * rng.integers(1, 70_000_000, size=1)[0]) % (2**32 - 1)
+        lists = [sorted(set(big[col_off[v]:col_off[v + 1]].tolist())) for v in range(n)]
+        co = np.zeros(n + 1, dtype=np.int64)
+        co[1:] = np.cumsum([len(x) for x in lists])
+        rw = np.array([u for x in lists for u in x], dtype=np.int64)
+        boff, data = oracle.pack_gaps(co, rw)
+        want = b"".join(oracle.leb128(x[0]) + b"".join(oracle.leb128(b - a - 1) for a, b in zip(x, x[1:]))
+                        if x else b"" for x in lists)
+        assert data.tobytes() == want
+        assert oracle.unpack_gaps(boff, data, n) == lists
+        assert boff[0] == 0 and boff[-1] == len(want)
+
+
 # ------------------------------------------------------------------ SSSP
 
 def floyd_warshall(n, src, dst, w):
