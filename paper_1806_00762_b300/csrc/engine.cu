@@ -317,31 +317,40 @@ struct Piece {
 
 // The 7-bit groups of 4 code bytes packed into 28 bits.
 __device__ __forceinline__ uint32_t leb_payload4(uint32_t w) {
-    return (w & 0x7Fu) | ((w >> 1) & 0x3F80u) | ((w >> 2) & 0x1FC000u) | ((w >> 3) & 0xFE00000u);
+    const uint32_t t = (w & 0x007F007Fu) | ((w & 0x7F007F00u) >> 1);  // byte pairs -> 14 bits
+    return (t & 0x3FFFu) | ((t >> 2) & 0xFFFC000u);
 }
 
-// Every code start of a piece decoded at once: the 7-bit groups of the 20
-// window bytes are packed into one bit stream (byte j's group at bit 7j), so
-// the code at byte j is the stream's bits [7j, 7j + 7L) with L = distance to
-// the first ending byte at or after j (the byte positions are compile-time
-// constants once unrolled).  lid[j] = sum of (value + 1) over the codes
-// starting at or before byte j, i.e. the id of the code at j relative to the
-// id before the piece.  Returns the piece's total.
+// Every code start of a piece decoded at once.  The 7-bit groups of the 20
+// window bytes are packed into one bit stream (byte j's group at bit 7j) and
+// their end flags into a second one (a code's last byte flags bit 7j + 6), so
+// the code starting at byte j is x & (e ^ (e - 1)) with x, e the 32 bits of
+// the two streams from bit 7j: the mask keeps everything up to the first end
+// flag (all 32 bits for a 5-byte code, whose value fits them exactly).  The
+// byte positions are compile-time constants once unrolled.  lid[j] = sum of
+// (value + 1) over the codes starting at or before byte j, i.e. the id of the
+// code at j relative to the id before the piece.  Returns the piece's total.
 __device__ __forceinline__ uint32_t piece_decode(const Piece& P, uint32_t st, uint32_t lid[16]) {
-    const uint32_t p0 = leb_payload4(P.w0), p1 = leb_payload4(P.w1), p2 = leb_payload4(P.w2),
-                   p3 = leb_payload4(P.w3), p4 = leb_payload4(P.w4);
-    const uint32_t sw[6] = {p0 | (p1 << 28), (p1 >> 4) | (p2 << 24), (p2 >> 8) | (p3 << 20),
-                            (p3 >> 12) | (p4 << 16), p4 >> 16, 0u};
-    const uint32_t ends = leb_ends4(P.w0) | (leb_ends4(P.w1) << 4) | (leb_ends4(P.w2) << 8) |
-                          (leb_ends4(P.w3) << 12) | (leb_ends4(P.w4) << 16);
+    const uint32_t w[5] = {P.w0, P.w1, P.w2, P.w3, P.w4};
+    uint32_t p[5], q[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        p[k] = leb_payload4(w[k]);
+        // end flags of the 4 bytes spread to bits 6, 13, 20, 27 (the product
+        // terms of distinct bits land on distinct bits: no carries)
+        q[k] = (leb_ends4(w[k]) * 0x01041040u) & 0x08102040u;
+    }
+    const uint32_t sw[6] = {p[0] | (p[1] << 28), (p[1] >> 4) | (p[2] << 24), (p[2] >> 8) | (p[3] << 20),
+                            (p[3] >> 12) | (p[4] << 16), p[4] >> 16, 0u};
+    const uint32_t se[6] = {q[0] | (q[1] << 28), (q[1] >> 4) | (q[2] << 24), (q[2] >> 8) | (q[3] << 20),
+                            (q[3] >> 12) | (q[4] << 16), q[4] >> 16, 0u};
     uint32_t acc = 0;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        const int o = 7 * j, o5 = o + 28;
+        const int o = 7 * j;
         const uint32_t x = __funnelshift_r(sw[o >> 5], sw[(o >> 5) + 1], o & 31);
-        const uint32_t L = __ffs(ends >> j);  // code length 1..5 (0 only for a corrupt stream)
-        uint32_t v = x & ((1u << (7u * (L < 4u ? L : 4u))) - 1u);
-        if (L == 5u) v |= __funnelshift_r(sw[o5 >> 5], sw[(o5 >> 5) + 1], o5 & 31) << 28;
+        const uint32_t e = __funnelshift_r(se[o >> 5], se[(o >> 5) + 1], o & 31);
+        const uint32_t v = x & (e ^ (e - 1u));
         acc += ((st >> j) & 1u) ? v + 1u : 0u;
         lid[j] = acc;
     }
