@@ -269,7 +269,7 @@ def main_batch(args, world, rank):
     raw_edges = sum(edges_of[g] for g, _, _ in queries)
     t = st["time_ms"] / 1e3
     # end to end: the public call with host outputs (query table in, distances out)
-    houts = [np.empty(graphs[g].n, dtype=np.uint32) for g, _, _ in queries]
+    houts = [torch.empty(graphs[g].n, dtype=torch.int32, pin_memory=True) for g, _, _ in queries]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -361,8 +361,9 @@ def main():
     setup_s = time.time() - t_setup
     link = link_gbps(torch)
     budget = int(args.budget_gb * (1 << 30))
-    out_u = np.empty(n, dtype=np.uint32)
-    out_f = np.empty(n, dtype=np.float32)
+    # results land in pinned host buffers (the end-to-end read-back of each run)
+    out_u = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    out_f = torch.empty(n, dtype=torch.float32, pin_memory=True)
 
     algos = args.algos.split(",")
     empty = {k: 0 for k in ("time_ms", "wall_ms", "relax_ms", "relax_launches", "bytes_streamed",
