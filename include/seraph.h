@@ -403,7 +403,11 @@ typedef struct seraph_batch_params {
     uint32_t use_graph;         /* 1: capture the launch in a CUDA graph      */
     uint32_t replays;           /* timed repetitions (>= 1)                   */
     uint32_t timeout_ms;        /* bound on every wait, device and host       */
-    uint32_t reserved;
+    uint32_t delta;             /* SSSP near-far bucket width (0 = 64): an
+                                   improved vertex whose distance is below the
+                                   current split joins the next round, the
+                                   rest wait in a far pile until the split
+                                   rises by delta; BFS ignores it            */
     void*    stream;            /* cudaStream_t, NULL = own                   */
 } seraph_batch_params;
 

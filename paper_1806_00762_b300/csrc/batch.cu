@@ -41,13 +41,25 @@ struct BGraphDev {
     uint32_t n, wbytes;
 };
 
+// SSSP queries order their work near-far: improved vertices whose distance is
+// below `split` join the next round's (near) frontier, the others a far pile
+// (once per epoch).  When the near frontier runs dry, a filter round raises
+// split to (smallest far distance) + delta and moves the far vertices now
+// below it to the near frontier, keeping the rest in the other far pile.
+// BFS queries keep split = infinity (plain level-synchronous push).
 struct BQuery {
     uint32_t graph, algo, source, mapping, tile;
     uint32_t round, cur_n, next_n, tiles_total, tiles_done, done, pad;
+    uint32_t split, delta, phase, fsel, epoch, far_min, far_n[2];
     uint32_t* dist;
     uint32_t* stamp;
     uint32_t* front[2];
+    uint32_t* far[2];
+    uint32_t* fstamp;
 };
+
+constexpr uint32_t kPhaseNear = 0, kPhaseFilter = 1;
+constexpr uint32_t kDefaultDelta = 64;  // near-far bucket width when the caller gives none
 
 struct BGlobal {
     unsigned long long head, tail, edges, tasks;
@@ -66,23 +78,43 @@ __device__ __forceinline__ uint32_t weight_at(const BGraphDev& g, uint64_t e) {
     return ((const uint32_t*)g.w)[e];
 }
 
-// Relax edge (u -> v) with candidate distance cand; push v on improvement.
-__device__ __forceinline__ bool relax(const BQuery& Q, uint32_t v, uint32_t cand) {
+constexpr int kPushNone = 0, kPushNear = 1, kPushFar = 2;
+
+// Relax edge (u -> v) with candidate distance cand.  `seen` is v's distance
+// as last read: a candidate that does not beat it takes no atomic (most
+// edges, and every edge into a hub that is already settled -- atomics on one
+// address would serialise in L2).  An improvement pushes v once per round to
+// the near frontier (cand < split) or once per epoch to the far pile.
+__device__ __forceinline__ int relax(const BQuery& Q, uint32_t v, uint32_t cand, uint32_t seen) {
+    if (cand >= seen) return kPushNone;
     const uint32_t old = atomicMin(&Q.dist[v], cand);
-    if (cand >= old) return false;
-    return atomicMax(&Q.stamp[v], Q.round + 1) < Q.round + 1;  // first push this round
+    if (cand >= old) return kPushNone;
+    if (cand < Q.split)
+        return atomicMax(&Q.stamp[v], Q.round + 1) < Q.round + 1 ? kPushNear : kPushNone;
+    return atomicMax(&Q.fstamp[v], Q.epoch + 1) < Q.epoch + 1 ? kPushFar : kPushNone;
 }
 
-// Warp-aggregated append of `push` lanes' vertices to q's next frontier.
-__device__ __forceinline__ void push_next(BQuery* qs, uint32_t q, const BQuery& Q, bool push,
-                                          uint32_t v) {
+// Warp-aggregated append of the `push` lanes' vertices to list[*count].
+__device__ __forceinline__ void append(uint32_t* list, uint32_t* count, bool push, uint32_t v) {
     const unsigned m = __ballot_sync(kFull, push);
     if (!m) return;
     const unsigned leader = __ffs(m) - 1;
     unsigned base = 0;
-    if (lane_id() == leader) base = atomicAdd(&qs[q].next_n, __popc(m));
+    if (lane_id() == leader) base = atomicAdd(count, __popc(m));
     base = __shfl_sync(kFull, base, leader);
-    if (push) Q.front[(Q.round + 1) & 1][base + __popc(m & lanemask_lt())] = v;
+    if (push) list[base + __popc(m & lanemask_lt())] = v;
+}
+
+// Near pushes go to the next round's frontier, far pushes to the current far
+// pile (whose smallest candidate is tracked); every lane of the warp calls.
+__device__ __forceinline__ void push_next(BQuery* qs, uint32_t q, const BQuery& Q, int push,
+                                          uint32_t v, uint32_t cand) {
+    append(Q.front[(Q.round + 1) & 1], &qs[q].next_n, push == kPushNear, v);
+    if (__any_sync(kFull, push == kPushFar)) {
+        append(Q.far[Q.fsel], &qs[q].far_n[Q.fsel], push == kPushFar, v);
+        const uint32_t mn = __reduce_min_sync(kFull, push == kPushFar ? cand : SERAPH_INF);
+        if (lane_id() == 0 && mn != SERAPH_INF) atomicMin(&qs[q].far_min, mn);
+    }
 }
 
 __device__ __forceinline__ uint32_t cand_of(const BQuery& Q, uint32_t du, uint32_t w, bool& ok) {
@@ -99,44 +131,99 @@ __device__ __forceinline__ BQuery load_query(const BQuery* p) {
     Q.graph = v->graph; Q.algo = v->algo; Q.source = v->source; Q.mapping = v->mapping;
     Q.tile = v->tile; Q.round = v->round; Q.cur_n = v->cur_n; Q.next_n = 0;
     Q.tiles_total = 0; Q.tiles_done = 0; Q.done = 0; Q.pad = 0;
+    Q.split = v->split; Q.delta = v->delta; Q.phase = v->phase; Q.fsel = v->fsel;
+    Q.epoch = v->epoch; Q.far_min = 0; Q.far_n[0] = Q.far_n[1] = 0;
     Q.dist = v->dist; Q.stamp = v->stamp; Q.front[0] = v->front[0]; Q.front[1] = v->front[1];
+    Q.far[0] = v->far[0]; Q.far[1] = v->far[1]; Q.fstamp = v->fstamp;
     return Q;
+}
+
+constexpr int kEdgeIlp = 4;  // edges per lane in flight per step
+
+// kEdgeIlp edges per lane: columns and weights first, then the distance
+// reads, then the atomics of the candidates that improve, then the pushes.
+// Edge j of this lane is (u_j -> col[e_j]) with source distance du_j; lanes
+// with act_j false carry nothing (but still take part in the ballots).
+__device__ __forceinline__ void relax_edges(BQuery* qs, uint32_t q, const BQuery& Q,
+                                            const BGraphDev& G, const bool act[kEdgeIlp],
+                                            const uint64_t e[kEdgeIlp],
+                                            const uint32_t du[kEdgeIlp]) {
+    uint32_t v[kEdgeIlp], c[kEdgeIlp], seen[kEdgeIlp];
+    bool ok[kEdgeIlp];
+#pragma unroll
+    for (int j = 0; j < kEdgeIlp; ++j) {
+        v[j] = act[j] ? G.col[e[j]] : 0u;
+        c[j] = act[j] ? cand_of(Q, du[j], weight_at(G, e[j]), ok[j]) : 0u;
+        ok[j] = act[j] && ok[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kEdgeIlp; ++j) seen[j] = ok[j] ? __ldcg(Q.dist + v[j]) : 0u;
+    int push[kEdgeIlp];
+#pragma unroll
+    for (int j = 0; j < kEdgeIlp; ++j) push[j] = ok[j] ? relax(Q, v[j], c[j], seen[j]) : kPushNone;
+#pragma unroll
+    for (int j = 0; j < kEdgeIlp; ++j) push_next(qs, q, Q, push[j], v[j], c[j]);
+}
+
+// A filter task: far-pile entries [t0, t0 + cnt) of query q.  Vertices whose
+// distance is now below split join the near frontier (once per round), the
+// others the other far pile (once per epoch).
+__device__ void filter_tile(BQuery* qs, uint32_t q, const BQuery& Q, uint32_t t0, uint32_t cnt) {
+    const uint32_t* src = Q.far[Q.fsel];
+    const uint32_t dst = Q.fsel ^ 1u;
+    for (uint32_t base = 0; base < cnt; base += kNT) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t v = 0, d = SERAPH_INF;
+        if (i < cnt) {
+            v = __ldcg(src + t0 + i);
+            d = __ldcg(Q.dist + v);
+        }
+        const bool near = i < cnt && d < Q.split &&
+                          atomicMax(&Q.stamp[v], Q.round + 1) < Q.round + 1;
+        const bool far = i < cnt && d >= Q.split &&
+                         atomicMax(&Q.fstamp[v], Q.epoch + 1) < Q.epoch + 1;
+        append(Q.front[(Q.round + 1) & 1], &qs[q].next_n, near, v);
+        append(Q.far[dst], &qs[q].far_n[dst], far, v);
+        const uint32_t mn = __reduce_min_sync(kFull, far ? d : SERAPH_INF);
+        if (lane_id() == 0 && mn != SERAPH_INF) atomicMin(&qs[q].far_min, mn);
+    }
 }
 
 // One task: tile `tile` of query q's current frontier.  Returns edges relaxed.
 // Frontier entries and distances are mutable across rounds: read via L2.
 __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, uint32_t q,
-                                           uint32_t tile, uint64_t* s_pref, uint32_t* s_u) {
+                                           uint32_t tile, uint64_t* s_pref, uint64_t* s_e0,
+                                           uint32_t* s_du) {
     const BQuery Q = load_query(qs + q);
     const BGraphDev G = graphs[Q.graph];
     const uint32_t* cur = Q.front[Q.round & 1];
     const uint32_t t0 = tile * Q.tile;
     const uint32_t cnt = min(Q.tile, Q.cur_n - t0);
     unsigned long long edges = 0;
+    if (Q.phase == kPhaseFilter) {
+        filter_tile(qs, q, Q, t0, cnt);
+        return 0;
+    }
     if (Q.mapping == SERAPH_MAP_THREAD) {
         for (uint32_t base = 0; base < cnt; base += kNT) {  // warps stay converged for the ballot
             const uint32_t i = base + threadIdx.x;
-            uint32_t u = 0, du = 0;
+            uint32_t du = 0;
             uint64_t b = 0, e = 0;
             if (i < cnt) {
-                u = __ldcg(cur + t0 + i);
+                const uint32_t u = __ldcg(cur + t0 + i);
                 du = __ldcg(Q.dist + u);
                 b = G.off[u];
                 e = G.off[u + 1];
             }
             edges += e - b;
-            for (uint64_t k = b;; ++k) {
-                const bool act = k < e;
-                if (!__any_sync(kFull, act)) break;
-                bool push = false;
-                uint32_t v = 0;
-                if (act) {
-                    v = G.col[k];
-                    bool ok;
-                    const uint32_t c = cand_of(Q, du, weight_at(G, k), ok);
-                    push = ok && relax(Q, v, c);
-                }
-                push_next(qs, q, Q, push, v);
+            for (uint64_t k = b;; k += kEdgeIlp) {
+                if (!__any_sync(kFull, k < e)) break;
+                bool act[kEdgeIlp];
+                uint64_t ek[kEdgeIlp];
+                uint32_t dk[kEdgeIlp];
+#pragma unroll
+                for (int j = 0; j < kEdgeIlp; ++j) { act[j] = k + j < e; ek[j] = k + j; dk[j] = du; }
+                relax_edges(qs, q, Q, G, act, ek, dk);
             }
         }
     } else if (Q.mapping == SERAPH_MAP_WARP) {
@@ -146,17 +233,17 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
             const uint32_t du = __ldcg(Q.dist + u);
             const uint64_t b = G.off[u], e = G.off[u + 1];
             if (lane == 0) edges += e - b;
-            for (uint64_t k0 = b; k0 < e; k0 += 32) {
-                const uint64_t k = k0 + lane;
-                bool push = false;
-                uint32_t v = 0;
-                if (k < e) {
-                    v = G.col[k];
-                    bool ok;
-                    const uint32_t c = cand_of(Q, du, weight_at(G, k), ok);
-                    push = ok && relax(Q, v, c);
+            for (uint64_t k0 = b; k0 < e; k0 += 32 * kEdgeIlp) {
+                bool act[kEdgeIlp];
+                uint64_t ek[kEdgeIlp];
+                uint32_t dk[kEdgeIlp];
+#pragma unroll
+                for (int j = 0; j < kEdgeIlp; ++j) {
+                    ek[j] = k0 + j * 32 + lane;
+                    act[j] = ek[j] < e;
+                    dk[j] = du;
                 }
-                push_next(qs, q, Q, push, v);
+                relax_edges(qs, q, Q, G, act, ek, dk);
             }
         }
     } else {  // edge-balanced over the tile (tile <= kMaxCtaTile)
@@ -166,8 +253,10 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
             uint64_t d = 0;
             if (i < cnt) {
                 const uint32_t u = __ldcg(cur + t0 + i);
-                s_u[i] = u;
-                d = G.off[u + 1] - G.off[u];
+                const uint64_t b = G.off[u];
+                s_e0[i] = b;
+                s_du[i] = __ldcg(Q.dist + u);
+                d = G.off[u + 1] - b;
             }
             uint64_t tot;
             const uint64_t ex = block_excl_scan<kNT>(d, ws, &tot);
@@ -178,31 +267,34 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
         }
         const uint64_t total = s_pref[cnt];
         edges = threadIdx.x == 0 ? total : 0;
-        for (uint64_t k0 = 0; k0 < total; k0 += kNT) {
-            const uint64_t k = k0 + threadIdx.x;
-            bool push = false;
-            uint32_t v = 0;
-            if (k < total) {
-                uint32_t lo = 0, hi = cnt - 1;  // largest i with s_pref[i] <= k
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) >> 1;
-                    if (s_pref[mid] <= k) lo = mid; else hi = mid - 1;
+        for (uint64_t k0 = 0; k0 < total; k0 += (uint64_t)kNT * kEdgeIlp) {
+            bool act[kEdgeIlp];
+            uint64_t ek[kEdgeIlp];
+            uint32_t dk[kEdgeIlp];
+#pragma unroll
+            for (int j = 0; j < kEdgeIlp; ++j) {
+                const uint64_t k = k0 + (uint64_t)j * kNT + threadIdx.x;
+                act[j] = k < total;
+                ek[j] = 0;
+                dk[j] = 0;
+                if (act[j]) {
+                    uint32_t lo = 0, hi = cnt - 1;  // largest i with s_pref[i] <= k
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (s_pref[mid] <= k) lo = mid; else hi = mid - 1;
+                    }
+                    ek[j] = s_e0[lo] + (k - s_pref[lo]);
+                    dk[j] = s_du[lo];
                 }
-                const uint32_t u = s_u[lo];
-                const uint64_t e = G.off[u] + (k - s_pref[lo]);
-                v = G.col[e];
-                bool ok;
-                const uint32_t c = cand_of(Q, __ldcg(Q.dist + u), weight_at(G, e), ok);
-                push = ok && relax(Q, v, c);
             }
-            push_next(qs, q, Q, push, v);
+            relax_edges(qs, q, Q, G, act, ek, dk);
         }
         __syncthreads();
     }
     return edges;
 }
 
-constexpr uint32_t kMaxCtaTile = 2048;
+constexpr uint32_t kMaxCtaTile = 1024;
 
 // Publish tasks [t0, t0 + count) = (q, tile 0..count-1); the whole block helps.
 __device__ bool publish(TaskSlot* ring, unsigned long long mask, unsigned long long t0,
@@ -231,7 +323,8 @@ __global__ void __launch_bounds__(kNT) batch_kernel(const BGraphDev* graphs, BQu
                                                     unsigned long long mask,
                                                     unsigned long long spin_limit) {
     __shared__ uint64_t s_pref[kMaxCtaTile + 1];
-    __shared__ uint32_t s_u[kMaxCtaTile];
+    __shared__ uint64_t s_e0[kMaxCtaTile];
+    __shared__ uint32_t s_du[kMaxCtaTile];
     __shared__ uint32_t s_q, s_tile, s_last, s_count;
     __shared__ int s_exit;
     __shared__ unsigned long long s_t0;
@@ -261,7 +354,7 @@ __global__ void __launch_bounds__(kNT) batch_kernel(const BGraphDev* graphs, BQu
         __syncthreads();
         if (s_exit) break;
         const uint32_t q = s_q;
-        const unsigned long long e = process_tile(graphs, qs, q, s_tile, s_pref, s_u);
+        const unsigned long long e = process_tile(graphs, qs, q, s_tile, s_pref, s_e0, s_du);
         atomicAdd(&s_edges, e);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -270,14 +363,29 @@ __global__ void __launch_bounds__(kNT) batch_kernel(const BGraphDev* graphs, BQu
             s_last = done == *(volatile uint32_t*)&qs[q].tiles_total;
             if (s_last) {  // advance query q to its next round
                 __threadfence();
-                BQuery* Q = &qs[q];
-                const uint32_t nn = *(volatile uint32_t*)&Q->next_n;
-                Q->round = *(volatile uint32_t*)&Q->round + 1;
+                volatile BQuery* Q = &qs[q];
+                if (Q->phase == kPhaseFilter) {  // the filter wrote the other far pile
+                    Q->fsel = Q->fsel ^ 1u;
+                    Q->phase = kPhaseNear;
+                }
+                uint32_t nn = Q->next_n;
+                if (nn == 0 && Q->far_n[Q->fsel] > 0) {  // near frontier dry: filter the far pile
+                    const uint32_t fs = Q->fsel;
+                    nn = Q->far_n[fs];
+                    const uint32_t lim = SERAPH_INF - 1u - Q->delta;
+                    Q->split = Q->far_min < lim ? Q->far_min + Q->delta : SERAPH_INF - 1u;
+                    Q->far_min = SERAPH_INF;
+                    Q->far_n[fs ^ 1u] = 0;
+                    Q->far_n[fs] = 0;  // read again through cur_n by the filter tasks
+                    Q->epoch = Q->epoch + 1;
+                    Q->phase = kPhaseFilter;
+                }
+                Q->round = Q->round + 1;
                 atomicMax(&gl->max_round, Q->round);
                 Q->cur_n = nn;
                 Q->next_n = 0;
                 Q->tiles_done = 0;
-                Q->tiles_total = (nn + *(volatile uint32_t*)&Q->tile - 1) / *(volatile uint32_t*)&Q->tile;
+                Q->tiles_total = (nn + Q->tile - 1) / Q->tile;
                 s_count = Q->tiles_total;
                 if (nn == 0) {
                     Q->done = 1;
@@ -305,6 +413,7 @@ __global__ void init_dist_kernel(BQuery* qs, const BGraphDev* graphs, uint32_t n
         for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
             Q.dist[v] = v == Q.source ? 0u : SERAPH_INF;
             Q.stamp[v] = 0;
+            if (Q.fstamp) Q.fstamp[v] = 0;
         }
     }
 }
@@ -326,6 +435,12 @@ __global__ void init_queries_kernel(BQuery* qs, uint32_t nq, BGlobal* gl, TaskSl
         Q.tiles_total = 1;
         Q.tiles_done = 0;
         Q.done = 0;
+        Q.split = Q.algo == SERAPH_SSSP ? Q.delta : SERAPH_INF;
+        Q.phase = kPhaseNear;
+        Q.fsel = 0;
+        Q.epoch = 0;
+        Q.far_min = SERAPH_INF;
+        Q.far_n[0] = Q.far_n[1] = 0;
         Q.front[0][0] = Q.source;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -342,6 +457,7 @@ __global__ void init_queries_kernel(BQuery* qs, uint32_t nq, BGlobal* gl, TaskSl
 struct QSpec {
     uint32_t graph, algo, source, mapping, tile;
     uint32_t* out;  // device buffer for the distances, or null
+    uint32_t delta; // near-far bucket width (SSSP)
 };
 
 struct Outcome {
@@ -378,7 +494,7 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
     }
     std::vector<BQuery> qh(nq);
     hold->clear();
-    hold->reserve(4 * (size_t)nq);
+    hold->reserve(7 * (size_t)nq);
     uint64_t tiles = 0;
     uint32_t max_n = 1;
     for (uint32_t q = 0; q < nq; ++q) {
@@ -396,6 +512,12 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
         hold->emplace_back(n); b.stamp = hold->back().p;
         hold->emplace_back(n); b.front[0] = hold->back().p;
         hold->emplace_back(n); b.front[1] = hold->back().p;
+        b.delta = Q.delta ? Q.delta : 1u;
+        if (Q.algo == SERAPH_SSSP) {  // far piles and their per-epoch stamps
+            hold->emplace_back(n); b.far[0] = hold->back().p;
+            hold->emplace_back(n); b.far[1] = hold->back().p;
+            hold->emplace_back(n); b.fstamp = hold->back().p;
+        }
         qh[q] = b;
         tiles += (n + Q.tile - 1) / Q.tile;
         if (dist_out) (*dist_out)[q] = b.dist;
@@ -490,6 +612,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
     SR_CHECK(out_mem == SERAPH_MEM_HOST || out_mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad out_mem");
     SR_CHECK(P->mapping >= SERAPH_MAP_AUTO && P->mapping <= SERAPH_MAP_CTA, SERAPH_EINVAL, "bad mapping");
     SR_CHECK(P->tile == 0 || (P->tile <= (1u << 20)), SERAPH_EINVAL, "bad tile");
+    const uint32_t delta = P->delta ? P->delta : kDefaultDelta;
     std::vector<seraph_bgraph*> graphs(graphs_in, graphs_in + ng);
     for (auto* g : graphs) SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
     SR_CUDA(cudaSetDevice(graphs[0]->device));
@@ -513,7 +636,8 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
         std::vector<QSpec> sub;
         std::vector<seraph_bgraph*> one{graphs[gi]};
         for (uint32_t q = 0; q < nq; ++q)
-            if (qin[q].graph == gi) sub.push_back(QSpec{0, (uint32_t)qin[q].algo, qin[q].source, 0, 0, nullptr});
+            if (qin[q].graph == gi)
+                sub.push_back(QSpec{0, (uint32_t)qin[q].algo, qin[q].source, 0, 0, nullptr, delta});
         float best = 1e30f;
         uint32_t bm = SERAPH_MAP_CTA, bt = 256;
         if (!sub.empty()) {
@@ -543,7 +667,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
         uint32_t tile = gtile[Q.graph];
         if (gmap[Q.graph] == SERAPH_MAP_CTA) tile = std::min<uint32_t>(tile, kMaxCtaTile);
         qs[q] = QSpec{Q.graph, algo, Q.source, gmap[Q.graph], tile,
-                      out_mem == SERAPH_MEM_DEVICE ? Q.out : nullptr};
+                      out_mem == SERAPH_MEM_DEVICE ? Q.out : nullptr, delta};
     }
     std::vector<uint32_t*> dist(nq);
     std::vector<DevBuf<uint32_t>> hold;

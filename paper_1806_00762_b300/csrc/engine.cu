@@ -925,14 +925,17 @@ __global__ void __launch_bounds__(kNT) pr_close_partial_kernel(const float* x, f
                                                                const float* inv_out, uint64_t n,
                                                                double* part_r, double* part_d) {
     __shared__ double ws[kNT / 32 + 1];
-    double r = 0.0, d = 0.0;
+    // per-thread partials (a few hundred terms) in compensated FP32 -- FP64
+    // arithmetic is scarce on this GPU -- then FP64 across threads and blocks
+    SumAcc rr{0.f, 0.f}, dd{0.f, 0.f};
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
         const float xv = x[v];
-        r += (double)fabsf(xv - x_prev[v]);
-        if (inv_out[v] == 0.0f) d += (double)xv;
+        sum_add<true>(rr, fabsf(xv - x_prev[v]));
+        if (inv_out[v] == 0.0f) sum_add<true>(dd, xv);
         x_prev[v] = xv;
     }
+    const double r = (double)rr.s - (double)rr.c, d = (double)dd.s - (double)dd.c;
     double tot;
     block_excl_scan<kNT>(r, ws, &tot);
     if (threadIdx.x == 0) part_r[blockIdx.x] = tot;

@@ -49,6 +49,18 @@ def test_batch_matches_oracle(work, kw):
         assert st["graph_captured"] == 1
 
 
+@pytest.mark.parametrize("delta", [1, 7, 64, 1000, 1 << 30])
+@pytest.mark.parametrize("mapping", ["thread", "warp", "cta"])
+def test_near_far_bucket_widths(work, delta, mapping):
+    """SSSP near-far ordering: any bucket width (1 = a filter round after
+    nearly every round, 2^30 = plain label-correcting rounds) gives the exact
+    distances."""
+    graphs, queries, refs = work
+    outs, st = seraph.batch_run(graphs, queries, mapping=mapping, tile=64, delta=delta)
+    for o, r in zip(outs, refs):
+        assert np.array_equal(o, r)
+
+
 def test_autotune_result_is_cached_and_device_outputs(work):
     import torch
     graphs, queries, refs = work
