@@ -65,6 +65,11 @@ def parse():
     ap.add_argument("--workload", default="streamed", choices=["streamed", "batch"],
                     help="streamed: the R-MAT-28 headline; batch: 256 BFS/SSSP queries over "
                          "16 resident R-MAT graphs (scales 14-22) in one persistent launch")
+    ap.add_argument("--batch-mapping", default="auto", choices=["auto", "thread", "warp", "cta"],
+                    help="batch: lane mapping of every graph (auto = the autotuner's choice)")
+    ap.add_argument("--batch-tile", type=int, default=0, help="batch: tile with a fixed mapping")
+    ap.add_argument("--batch-graph", type=int, default=-1,
+                    help="batch: keep only the queries of this graph (profiling one graph)")
     ap.add_argument("--algos", default="sssp,pagerank",
                     help="algorithms of a step (profiling runs may use one)")
     ap.add_argument("--cpu-scale", type=int, default=22, help="R-MAT scale of the CPU-oracle sample")
@@ -260,12 +265,17 @@ def main_batch(args, world, rank):
     import synth
     import paper_1806_00762_b300 as seraph
     graphs, queries, edges_of, specs = build_batch(seraph, synth, torch)
+    if args.batch_graph >= 0:
+        queries = [q for q in queries if q[0] == args.batch_graph]
+    kw = dict(mapping=args.batch_mapping)
+    if args.batch_tile:
+        kw["tile"] = args.batch_tile
     outs = [torch.empty(graphs[g].n, dtype=torch.int32, device="cuda") for g, _, _ in queries]
-    _, tune = seraph.batch_run(graphs, queries, outs=outs, mapping="auto")  # autotune (cached)
+    _, tune = seraph.batch_run(graphs, queries, outs=outs, **kw)  # autotune (cached)
     for _ in range(args.warmup):
-        seraph.batch_run(graphs, queries, outs=outs, mapping="auto")
+        seraph.batch_run(graphs, queries, outs=outs, **kw)
     with ClockSampler(0) as clk:
-        _, st = seraph.batch_run(graphs, queries, outs=outs, mapping="auto", replays=args.steps)
+        _, st = seraph.batch_run(graphs, queries, outs=outs, replays=args.steps, **kw)
     raw_edges = sum(edges_of[g] for g, _, _ in queries)
     t = st["time_ms"] / 1e3
     # end to end: the public call with host outputs (query table in, distances out)
@@ -273,7 +283,7 @@ def main_batch(args, world, rank):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        seraph.batch_run(graphs, queries, outs=houts, mapping="auto")
+        seraph.batch_run(graphs, queries, outs=houts, **kw)
     te2e = (time.perf_counter() - t0) / args.steps
     d2h = sum(4 * graphs[g].n for g, _, _ in queries)
     peaks = {}
@@ -292,7 +302,8 @@ def main_batch(args, world, rank):
             "value": len(queries) / t, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": st["time_ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "batch-256q-16g-rmat14-22", "graphs": specs,
+            "config": {"workload": "batch-256q-16g-rmat14-22" if args.batch_graph < 0 else
+                       f"batch-graph{args.batch_graph}-{len(queries)}q", "graphs": specs,
                        "queries": len(queries), "cuda_graph": bool(st["graph_captured"]),
                        "mapping": st["mapping"], "tile": st["tile"],
                        "l2": "inputs larger than L2: all 16 graphs resident, about "

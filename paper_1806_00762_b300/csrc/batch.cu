@@ -318,7 +318,9 @@ __device__ bool publish(TaskSlot* ring, unsigned long long mask, unsigned long l
     return ok;
 }
 
-__global__ void __launch_bounds__(kNT) batch_kernel(const BGraphDev* graphs, BQuery* qs,
+// Four resident CTAs per SM (<= 64 registers): the grid is 4 x SMs and the
+// kernel keeps no CTA waiting for a slot.
+__global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, BQuery* qs,
                                                     BGlobal* gl, TaskSlot* ring,
                                                     unsigned long long mask,
                                                     unsigned long long spin_limit) {
