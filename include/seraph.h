@@ -239,9 +239,11 @@ typedef struct seraph_params {
                                    evict-last priority and streamed page data
                                    with evict-first, so the most-read values
                                    stay in L2 (pair with SERAPH_REORDER, which
-                                   puts them first).  0 = no hints; the
-                                   default SERAPH_L2_HOT_AUTO = half the
-                                   device's L2.  Never changes a result.      */
+                                   puts them first); the run raises the
+                                   context's persisting-L2 limit to that size
+                                   and restores it on return.  0 = no hints;
+                                   the default SERAPH_L2_HOT_AUTO = 3/8 of
+                                   the device's L2.  Never changes a result. */
 } seraph_params;
 
 #define SERAPH_L2_HOT_AUTO UINT64_MAX
