@@ -140,3 +140,18 @@ def test_learned_schedule_results(r13, trained, which, algo):
 def test_learned_schedule_needs_window_one(r13, trained):
     with pytest.raises(seraph.SeraphError, match="EINVAL"):
         seraph.run(r13["g"], "sssp", window=2, sched_model=trained)
+
+
+@pytest.mark.parametrize("algo", ["sssp", "bfs"])
+def test_trained_network_gain_over_the_pipeline_without_it(r13, trained, algo):
+    """What the trained network buys: against the same pipeline without it
+    running the passes it was trained on (up to 16 per step, a pass stopping
+    only when the previous one changed nothing), the learned pass limit relaxes
+    fewer edges and runs fewer passes, with bit-identical results."""
+    g = r13["g"]
+    kw = dict(source=5, window=1, slots=6, budget_bytes=_budget(g, 6, use_w=algo == "sssp"))
+    base, sb = seraph.run(g, algo, passes=16, **kw)
+    got, sl = seraph.run(g, algo, sched_model=trained, **kw)
+    assert np.array_equal(base, r13[algo]) and np.array_equal(got, r13[algo])
+    assert sl["passes_run"] < sb["passes_run"]
+    assert sl["edges_relaxed"] < sb["edges_relaxed"]
