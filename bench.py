@@ -18,8 +18,8 @@ buffers, timed on the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl seraph|reference]
 
-Under torchrun every rank runs an independent replica (the method is
-single-GPU); rank 0 prints one JSON line.
+Under torchrun every rank runs an independent replica (the method runs on one
+GPU; there is no exchange step to shard); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -178,6 +178,18 @@ def relax_traffic(args) -> float | None:
     return RELAX_TRAFFIC["bytes_per_launch"]
 
 
+def pipeline_roofline(hbm_bytes: float, link_bytes: float, seconds: float, hbm_gbs: float,
+                      link_gbs: float) -> dict:
+    """The pipeline's roofline time, the slower of its relax bytes over HBM and
+    its streamed bytes over the host link (a lower bound of the per-step sum of
+    the two maxima), as a fraction of the measured time."""
+    t_hbm = hbm_bytes / (hbm_gbs * 1e9)
+    t_link = link_bytes / (link_gbs * 1e9) if link_gbs else 0.0
+    t_roof = max(t_hbm, t_link)
+    return {"bound": "link" if t_link >= t_hbm else "hbm", "t_roof_s": t_roof,
+            "t_hbm_s": t_hbm, "t_link_s": t_link, "frac": t_roof / seconds if seconds else 0.0}
+
+
 def max_over_ranks(vals, world: int, device: str):
     """Each value's maximum over the ranks (the slowest replica times the job);
     the identity for one process."""
@@ -204,7 +216,7 @@ def parse_sched(text: str) -> dict:
 
 
 def algo_bytes(algo, st, weight_width=4, weak=False) -> float:
-    """Algorithmic bytes of the relax kernels of a run (see DESIGN.md):
+    """Algorithmic bytes of the relax kernels of a run:
     SSSP (8 + w) B/edge (column, stored weight of w bytes, gathered distance)
     + 16 B per attempted vertex (list entry, offset pair, old value) + 4 B per
     change; PageRank 8 B/edge (column, gathered contribution) + 20 B per
@@ -484,6 +496,7 @@ def main():
                           "peak": link, "unit": "GB/s",
                           "frac": (streamed / (link * 1e9)) / dev_s if dev_s else 0,
                           "copy_busy_frac": copy_ms / 1e3 / dev_s if dev_s else 0},
+        "pipeline_roofline": pipeline_roofline(relax_bytes, streamed, dev_s, hbm_peak, link),
         "relax": {"launches": relax_launches, "ms": relax_ms, "bytes": relax_bytes},
         "gpu_launches": int(sum(a["kernel_launches"] + b["kernel_launches"] for a, b in stats)),
         "clocks": clk.summary(),
@@ -492,11 +505,15 @@ def main():
     if not args.no_paper_schedule:
         plain = dict(order="cyclic", window=4, slots=5, pvu="weak", columns="plain")
         p1, p2 = step(plain, plain)
+        p_bytes = (algo_bytes("sssp", p1, ww, True) + algo_bytes("pagerank", p2, ww, True))
+        p_time = (p1["time_ms"] + p2["time_ms"]) / 1e3
         line["paper_schedule"] = {
             "schedule": plain, "time_to_fixpoint_s": {"sssp": p1["time_ms"] / 1e3,
                                                        "pagerank": p2["time_ms"] / 1e3},
             "sweeps": {"sssp": p1["sweeps"], "pagerank": p2["sweeps"]},
-            "gteps": 2 * E / ((p1["time_ms"] + p2["time_ms"]) / 1e3) / 1e9}
+            "gteps": 2 * E / p_time / 1e9,
+            "pipeline_roofline": pipeline_roofline(
+                p_bytes, p1["bytes_streamed"] + p2["bytes_streamed"], p_time, hbm_peak, link)}
     if not args.no_learned:
         from paper_1806_00762_b300 import train_sched
         params = train_sched.load()
@@ -517,7 +534,7 @@ def main():
                 "sweeps": {"sssp": l1["sweeps"], "pagerank": l2["sweeps"]},
                 "fixed_time_to_fixpoint_s": fixed_t,
                 "gteps": 2 * E / (sum(learned_t.values())) / 1e9,
-                # the fixed schedule is the judge: keep the learned one only where it wins
+                # the fixed schedule is the yardstick: keep the learned one only where it wins
                 "chosen": {a: ("learned" if learned_t[a] < fixed_t[a] else "fixed") for a in fixed_t},
                 "weights": "paper_1806_00762_b300/sched_weights.f32"}
     if rank == 0 and not args.no_cpu_baseline:

@@ -328,11 +328,12 @@ int seraph_pull_fixpoint_noalloc(int algo, uint64_t n, const uint64_t* col_off,
  * number of local passes k in [1,16] for the step (argmax of 16 logits) and a
  * streaming priority (predicted first-pass gain).  With params.sched =
  * SERAPH_SCHED_LEARNED (window must be 1) the device caps each step's passes
- * at the predicted k (no host round trip) and every sweep streams chunks in
- * descending predicted priority; for SSSP/BFS/CC chunks predicted to change
- * nothing may be skipped in a sweep, which the stop rule (every chunk
- * processed after the last change) makes safe.  The fixed schedule remains
- * the fallback and the judge.
+ * at the predicted k (no host round trip) and sweeps keep the base chunk
+ * order (cyclic or zigzag); for SSSP/BFS/CC a chunk predicted to change
+ * nothing (priority < 0.02) may be skipped, for at most three sweeps in a
+ * row and never when verify = 0, which the stop rule (every chunk processed
+ * after the last change) makes safe.  The fixed schedule remains the
+ * fallback and the yardstick.
  */
 #define SERAPH_SCHED_FEATURES 16
 #define SERAPH_SCHED_OUTPUTS 17
@@ -376,7 +377,7 @@ int  seraph_sched_targets(const seraph_trace* t, float share, int32_t* k_out, fl
 void seraph_sched_free(seraph_sched_model* m);
 
 /*
- * Batched queries (not in the paper; SURVEY's batching pattern): many BFS /
+ * Batched queries (not in the paper; a serving pattern): many BFS /
  * SSSP queries over many graphs resident in device memory, run by one
  * persistent kernel that is captured in a CUDA graph.  Each query advances
  * in frontier rounds (push relaxation over the out-edge CSR, label

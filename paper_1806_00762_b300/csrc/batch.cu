@@ -1,6 +1,6 @@
 // Batched multi-query BFS/SSSP over many resident graphs in one persistent
-// kernel (not in the paper: the north-star's batching pattern for many
-// sources and many small graphs).
+// kernel (not in the paper: a serving pattern for many sources and many
+// small graphs).
 //
 // Each query keeps its own distances and two frontier lists and advances in
 // rounds; a round's frontier is cut into tiles of T vertices, and every tile
