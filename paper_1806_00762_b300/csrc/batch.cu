@@ -68,7 +68,20 @@ struct BGlobal {
 
 struct TaskSlot {
     unsigned long long seq;  // task index + 1 once published, kConsumed once read, 0 initially
-    uint32_t q, tile;
+    uint32_t q, tile, part, pad;
+};
+
+// A CTA-mapped tile whose frontier vertices have more than kPartEdges out-edges
+// in all is processed in parts of kPartEdges edges: the task of part 0 spawns
+// the others into the ring (raising the round's task count before its own
+// completion is counted), so one hub no longer holds a round to one CTA.
+constexpr uint64_t kPartEdges = 16384;
+
+// What a task needs to spawn further tasks.
+struct RingCtx {
+    TaskSlot* ring;
+    unsigned long long mask, spin_limit;
+    BGlobal* gl;
 };
 
 __device__ __forceinline__ uint32_t weight_at(const BGraphDev& g, uint64_t e) {
@@ -106,15 +119,13 @@ __device__ __forceinline__ void append(uint32_t* list, uint32_t* count, bool pus
 }
 
 // Near pushes go to the next round's frontier, far pushes to the current far
-// pile (whose smallest candidate is tracked); every lane of the warp calls.
+// pile; every lane of the warp calls.  (The far pile's minimum is taken only
+// by filter rounds: every far push is >= split, so split + delta is a safe
+// next split when it is unknown.)
 __device__ __forceinline__ void push_next(BQuery* qs, uint32_t q, const BQuery& Q, int push,
-                                          uint32_t v, uint32_t cand) {
+                                          uint32_t v) {
     append(Q.front[(Q.round + 1) & 1], &qs[q].next_n, push == kPushNear, v);
-    if (__any_sync(kFull, push == kPushFar)) {
-        append(Q.far[Q.fsel], &qs[q].far_n[Q.fsel], push == kPushFar, v);
-        const uint32_t mn = __reduce_min_sync(kFull, push == kPushFar ? cand : SERAPH_INF);
-        if (lane_id() == 0 && mn != SERAPH_INF) atomicMin(&qs[q].far_min, mn);
-    }
+    if (__any_sync(kFull, push == kPushFar)) append(Q.far[Q.fsel], &qs[q].far_n[Q.fsel], push == kPushFar, v);
 }
 
 __device__ __forceinline__ uint32_t cand_of(const BQuery& Q, uint32_t du, uint32_t w, bool& ok) {
@@ -162,7 +173,7 @@ __device__ __forceinline__ void relax_edges(BQuery* qs, uint32_t q, const BQuery
 #pragma unroll
     for (int j = 0; j < kEdgeIlp; ++j) push[j] = ok[j] ? relax(Q, v[j], c[j], seen[j]) : kPushNone;
 #pragma unroll
-    for (int j = 0; j < kEdgeIlp; ++j) push_next(qs, q, Q, push[j], v[j], c[j]);
+    for (int j = 0; j < kEdgeIlp; ++j) push_next(qs, q, Q, push[j], v[j]);
 }
 
 // A filter task: far-pile entries [t0, t0 + cnt) of query q.  Vertices whose
@@ -189,11 +200,36 @@ __device__ void filter_tile(BQuery* qs, uint32_t q, const BQuery& Q, uint32_t t0
     }
 }
 
+// Publish tasks [t0, t0 + count) of query q; the whole block helps.  Task i
+// is tile i, part 0 (a round), or tile `tile`, part i + 1 (spawned parts).
+__device__ bool publish(TaskSlot* ring, unsigned long long mask, unsigned long long t0,
+                        uint32_t count, uint32_t q, unsigned long long spin_limit,
+                        bool parts = false, uint32_t tile = 0) {
+    bool ok = true;
+    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+        TaskSlot* sl = &ring[(t0 + i) & mask];
+        unsigned long long spins = 0;
+        for (;;) {  // the slot's previous task must have been read
+            const unsigned long long s = *(volatile unsigned long long*)&sl->seq;
+            if (s == 0 || s == kConsumed) break;
+            if (++spins > spin_limit) { ok = false; break; }
+            __nanosleep(32);
+        }
+        if (!ok) break;
+        sl->q = q;
+        sl->tile = parts ? tile : i;
+        sl->part = parts ? i + 1 : 0;
+        __threadfence();
+        *(volatile unsigned long long*)&sl->seq = t0 + i + 1;
+    }
+    return ok;
+}
+
 // One task: tile `tile` of query q's current frontier.  Returns edges relaxed.
 // Frontier entries and distances are mutable across rounds: read via L2.
 __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, uint32_t q,
-                                           uint32_t tile, uint64_t* s_pref, uint64_t* s_e0,
-                                           uint32_t* s_du) {
+                                           uint32_t tile, uint32_t part, const RingCtx& rc,
+                                           uint64_t* s_pref, uint64_t* s_e0, uint32_t* s_du) {
     const BQuery Q = load_query(qs + q);
     const BGraphDev G = graphs[Q.graph];
     const uint32_t* cur = Q.front[Q.round & 1];
@@ -266,15 +302,31 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
             __syncthreads();
         }
         const uint64_t total = s_pref[cnt];
-        edges = threadIdx.x == 0 ? total : 0;
-        for (uint64_t k0 = 0; k0 < total; k0 += (uint64_t)kNT * kEdgeIlp) {
+        const uint64_t lo = (uint64_t)part * kPartEdges;
+        const uint64_t hi = total < lo + kPartEdges ? total : lo + kPartEdges;
+        if (part == 0 && total > kPartEdges) {  // spawn parts 1.. of this tile
+            __shared__ unsigned long long s_t0;
+            __shared__ uint32_t s_n;
+            if (threadIdx.x == 0) {
+                s_n = (uint32_t)((total - 1) / kPartEdges);
+                atomicAdd(&qs[q].tiles_total, s_n);  // before this task counts as done
+                s_t0 = atomicAdd(&rc.gl->tail, (unsigned long long)s_n);
+                atomicAdd(&rc.gl->tasks, (unsigned long long)s_n);
+            }
+            __syncthreads();
+            if (!publish(rc.ring, rc.mask, s_t0, s_n, q, rc.spin_limit, true, tile))
+                atomicOr(&rc.gl->err, 4u);
+            __syncthreads();
+        }
+        edges = threadIdx.x == 0 ? hi - lo : 0;
+        for (uint64_t k0 = lo; k0 < hi; k0 += (uint64_t)kNT * kEdgeIlp) {
             bool act[kEdgeIlp];
             uint64_t ek[kEdgeIlp];
             uint32_t dk[kEdgeIlp];
 #pragma unroll
             for (int j = 0; j < kEdgeIlp; ++j) {
                 const uint64_t k = k0 + (uint64_t)j * kNT + threadIdx.x;
-                act[j] = k < total;
+                act[j] = k < hi;
                 ek[j] = 0;
                 dk[j] = 0;
                 if (act[j]) {
@@ -297,27 +349,6 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
 constexpr uint32_t kMaxCtaTile = 1024;
 
 // Publish tasks [t0, t0 + count) = (q, tile 0..count-1); the whole block helps.
-__device__ bool publish(TaskSlot* ring, unsigned long long mask, unsigned long long t0,
-                        uint32_t count, uint32_t q, unsigned long long spin_limit) {
-    bool ok = true;
-    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
-        TaskSlot* sl = &ring[(t0 + i) & mask];
-        unsigned long long spins = 0;
-        for (;;) {  // the slot's previous task must have been read
-            const unsigned long long s = *(volatile unsigned long long*)&sl->seq;
-            if (s == 0 || s == kConsumed) break;
-            if (++spins > spin_limit) { ok = false; break; }
-            __nanosleep(32);
-        }
-        if (!ok) break;
-        sl->q = q;
-        sl->tile = i;
-        __threadfence();
-        *(volatile unsigned long long*)&sl->seq = t0 + i + 1;
-    }
-    return ok;
-}
-
 // Four resident CTAs per SM (<= 64 registers): the grid is 4 x SMs and the
 // kernel keeps no CTA waiting for a slot.
 __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, BQuery* qs,
@@ -327,7 +358,8 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
     __shared__ uint64_t s_pref[kMaxCtaTile + 1];
     __shared__ uint64_t s_e0[kMaxCtaTile];
     __shared__ uint32_t s_du[kMaxCtaTile];
-    __shared__ uint32_t s_q, s_tile, s_last, s_count;
+    __shared__ uint32_t s_q, s_tile, s_part, s_last, s_count;
+    const RingCtx rc{ring, mask, spin_limit, gl};
     __shared__ int s_exit;
     __shared__ unsigned long long s_t0;
     __shared__ unsigned long long s_edges;
@@ -344,6 +376,7 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
                     __threadfence();
                     s_q = sl->q;
                     s_tile = sl->tile;
+                    s_part = sl->part;
                     *(volatile unsigned long long*)&sl->seq = kConsumed;
                     break;
                 }
@@ -356,7 +389,7 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
         __syncthreads();
         if (s_exit) break;
         const uint32_t q = s_q;
-        const unsigned long long e = process_tile(graphs, qs, q, s_tile, s_pref, s_e0, s_du);
+        const unsigned long long e = process_tile(graphs, qs, q, s_tile, s_part, rc, s_pref, s_e0, s_du);
         atomicAdd(&s_edges, e);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -366,16 +399,19 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
             if (s_last) {  // advance query q to its next round
                 __threadfence();
                 volatile BQuery* Q = &qs[q];
+                bool exact_min = false;  // far_min is the current far pile's minimum
                 if (Q->phase == kPhaseFilter) {  // the filter wrote the other far pile
                     Q->fsel = Q->fsel ^ 1u;
                     Q->phase = kPhaseNear;
+                    exact_min = true;
                 }
                 uint32_t nn = Q->next_n;
                 if (nn == 0 && Q->far_n[Q->fsel] > 0) {  // near frontier dry: filter the far pile
                     const uint32_t fs = Q->fsel;
                     nn = Q->far_n[fs];
+                    const uint32_t base = exact_min ? Q->far_min : Q->split;
                     const uint32_t lim = SERAPH_INF - 1u - Q->delta;
-                    Q->split = Q->far_min < lim ? Q->far_min + Q->delta : SERAPH_INF - 1u;
+                    Q->split = base < lim ? base + Q->delta : SERAPH_INF - 1u;
                     Q->far_min = SERAPH_INF;
                     Q->far_n[fs ^ 1u] = 0;
                     Q->far_n[fs] = 0;  // read again through cur_n by the filter tasks
@@ -428,6 +464,7 @@ __global__ void init_queries_kernel(BQuery* qs, uint32_t nq, BGlobal* gl, TaskSl
         ring[i].seq = i < nq ? i + 1 : 0;
         ring[i].q = (uint32_t)i;
         ring[i].tile = 0;
+        ring[i].part = 0;
     }
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         BQuery& Q = qs[q];
@@ -521,7 +558,7 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
             hold->emplace_back(n); b.fstamp = hold->back().p;
         }
         qh[q] = b;
-        tiles += (n + Q.tile - 1) / Q.tile;
+        tiles += (n + Q.tile - 1) / Q.tile + graphs[Q.graph]->adj.E / kPartEdges + 1;
         if (dist_out) (*dist_out)[q] = b.dist;
     }
     const int sms = device_sms();
