@@ -118,14 +118,28 @@ __device__ __forceinline__ void append(uint32_t* list, uint32_t* count, bool pus
     if (push) list[base + __popc(m & lanemask_lt())] = v;
 }
 
-// Near pushes go to the next round's frontier, far pushes to the current far
-// pile; every lane of the warp calls.  (The far pile's minimum is taken only
-// by filter rounds: every far push is >= split, so split + delta is a safe
-// next split when it is unknown.)
-__device__ __forceinline__ void push_next(BQuery* qs, uint32_t q, const BQuery& Q, int push,
-                                          uint32_t v) {
-    append(Q.front[(Q.round + 1) & 1], &qs[q].next_n, push == kPushNear, v);
-    if (__any_sync(kFull, push == kPushFar)) append(Q.far[Q.fsel], &qs[q].far_n[Q.fsel], push == kPushFar, v);
+constexpr int kEdgeIlp = 4;  // edges per lane in flight per step
+static_assert(kEdgeIlp == 4, "relax_edges tests four far-push slots");
+
+// Warp-aggregated append of the kEdgeIlp slots of every lane whose push kind
+// is `kind`: one atomic per warp for all of them.
+__device__ __forceinline__ void append_many(uint32_t* list, uint32_t* count, const int push[kEdgeIlp],
+                                            int kind, const uint32_t v[kEdgeIlp]) {
+    unsigned m[kEdgeIlp], tot = 0;
+#pragma unroll
+    for (int j = 0; j < kEdgeIlp; ++j) {
+        m[j] = __ballot_sync(kFull, push[j] == kind);
+        tot += __popc(m[j]);
+    }
+    if (!tot) return;
+    unsigned base = 0;
+    if (lane_id() == 0) base = atomicAdd(count, tot);
+    base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+    for (int j = 0; j < kEdgeIlp; ++j) {
+        if (push[j] == kind) list[base + __popc(m[j] & lanemask_lt())] = v[j];
+        base += __popc(m[j]);
+    }
 }
 
 __device__ __forceinline__ uint32_t cand_of(const BQuery& Q, uint32_t du, uint32_t w, bool& ok) {
@@ -149,12 +163,48 @@ __device__ __forceinline__ BQuery load_query(const BQuery* p) {
     return Q;
 }
 
-constexpr int kEdgeIlp = 4;  // edges per lane in flight per step
 
 // kEdgeIlp edges per lane: columns and weights first, then the distance
 // reads, then the atomics of the candidates that improve, then the pushes.
 // Edge j of this lane is (u_j -> col[e_j]) with source distance du_j; lanes
 // with act_j false carry nothing (but still take part in the ballots).
+// Block-aggregated append (all threads of the block call): one atomic per
+// block for the near and far pushes of all its warps.
+__device__ __forceinline__ void append_block(BQuery* qs, uint32_t q, const BQuery& Q,
+                                             const int push[kEdgeIlp], const uint32_t v[kEdgeIlp]) {
+    __shared__ unsigned s_cnt[2][kNT / 32], s_base[2];
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    unsigned mn[kEdgeIlp], mf[kEdgeIlp], tn = 0, tf = 0;
+#pragma unroll
+    for (int j = 0; j < kEdgeIlp; ++j) {
+        mn[j] = __ballot_sync(kFull, push[j] == kPushNear);
+        mf[j] = __ballot_sync(kFull, push[j] == kPushFar);
+        tn += __popc(mn[j]);
+        tf += __popc(mf[j]);
+    }
+    if (lane == 0) { s_cnt[0][warp] = tn; s_cnt[1][warp] = tf; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        unsigned tot = 0;
+        for (int w = 0; w < kNT / 32; ++w) tot += s_cnt[threadIdx.x][w];
+        s_base[threadIdx.x] = tot ? atomicAdd(threadIdx.x == 0 ? &qs[q].next_n : &qs[q].far_n[Q.fsel], tot) : 0u;
+    }
+    __syncthreads();
+    unsigned bn = s_base[0], bf = s_base[1];
+    for (unsigned w = 0; w < warp; ++w) { bn += s_cnt[0][w]; bf += s_cnt[1][w]; }
+    uint32_t* near = Q.front[(Q.round + 1) & 1];
+    uint32_t* far = Q.far[Q.fsel];
+#pragma unroll
+    for (int j = 0; j < kEdgeIlp; ++j) {
+        if (push[j] == kPushNear) near[bn + __popc(mn[j] & lanemask_lt())] = v[j];
+        if (push[j] == kPushFar) far[bf + __popc(mf[j] & lanemask_lt())] = v[j];
+        bn += __popc(mn[j]);
+        bf += __popc(mf[j]);
+    }
+    __syncthreads();  // s_cnt is reused by the next call
+}
+
+template <bool BLOCK>
 __device__ __forceinline__ void relax_edges(BQuery* qs, uint32_t q, const BQuery& Q,
                                             const BGraphDev& G, const bool act[kEdgeIlp],
                                             const uint64_t e[kEdgeIlp],
@@ -172,8 +222,14 @@ __device__ __forceinline__ void relax_edges(BQuery* qs, uint32_t q, const BQuery
     int push[kEdgeIlp];
 #pragma unroll
     for (int j = 0; j < kEdgeIlp; ++j) push[j] = ok[j] ? relax(Q, v[j], c[j], seen[j]) : kPushNone;
-#pragma unroll
-    for (int j = 0; j < kEdgeIlp; ++j) push_next(qs, q, Q, push[j], v[j]);
+    if (BLOCK) {
+        append_block(qs, q, Q, push, v);
+        return;
+    }
+    append_many(Q.front[(Q.round + 1) & 1], &qs[q].next_n, push, kPushNear, v);
+    if (__any_sync(kFull, push[0] == kPushFar || push[1] == kPushFar || push[2] == kPushFar ||
+                              push[3] == kPushFar))
+        append_many(Q.far[Q.fsel], &qs[q].far_n[Q.fsel], push, kPushFar, v);
 }
 
 // A filter task: far-pile entries [t0, t0 + cnt) of query q.  Vertices whose
@@ -259,7 +315,7 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
                 uint32_t dk[kEdgeIlp];
 #pragma unroll
                 for (int j = 0; j < kEdgeIlp; ++j) { act[j] = k + j < e; ek[j] = k + j; dk[j] = du; }
-                relax_edges(qs, q, Q, G, act, ek, dk);
+                relax_edges<false>(qs, q, Q, G, act, ek, dk);
             }
         }
     } else if (Q.mapping == SERAPH_MAP_WARP) {
@@ -279,7 +335,7 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
                     act[j] = ek[j] < e;
                     dk[j] = du;
                 }
-                relax_edges(qs, q, Q, G, act, ek, dk);
+                relax_edges<false>(qs, q, Q, G, act, ek, dk);
             }
         }
     } else {  // edge-balanced over the tile (tile <= kMaxCtaTile)
@@ -339,7 +395,7 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
                     dk[j] = s_du[lo];
                 }
             }
-            relax_edges(qs, q, Q, G, act, ek, dk);
+            relax_edges<true>(qs, q, Q, G, act, ek, dk);
         }
         __syncthreads();
     }
