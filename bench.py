@@ -60,6 +60,10 @@ def parse():
                     help="degree: vertices numbered by non-increasing out-degree before the "
                          "page cut (SERAPH_REORDER); natural: the generator's ids")
     ap.add_argument("--no-paper-schedule", action="store_true")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also run the paper's ablation ladder (Fig. 9 style) on the same graph: "
+                         "baseline, pipelined subgraph iteration, + predictive updating, + this "
+                         "build's residency/packing")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-scheduler comparison run")
     ap.add_argument("--workload", default="streamed", choices=["streamed", "batch"],
@@ -514,6 +518,30 @@ def main():
             "gteps": 2 * E / p_time / 1e9,
             "pipeline_roofline": pipeline_roofline(
                 p_bytes, p1["bytes_streamed"] + p2["bytes_streamed"], p_time, hbm_peak, link)}
+    if args.ablation:
+        # baseline: one pass per streamed page pair (double buffer, no reuse), no prediction;
+        # psi: k = 4 local passes over a window of 4 chunks while the next streams (Fig. 4);
+        # psi+pvu: with the predictive vertex update (strong for SSSP, weak for PageRank);
+        # then this build's schedule without and with packed SSSP pages.
+        ladder = [
+            ("baseline", dict(order="cyclic", window=1, slots=2, pvu="off", columns="plain"),
+             dict(order="cyclic", window=1, slots=2, pvu="off", columns="plain")),
+            ("psi", dict(order="cyclic", window=4, slots=5, pvu="off", columns="plain"),
+             dict(order="cyclic", window=4, slots=5, pvu="off", columns="plain")),
+            ("psi+pvu", dict(order="cyclic", window=4, slots=5, pvu="strong", columns="plain"),
+             dict(order="cyclic", window=4, slots=5, pvu="weak", columns="plain")),
+            ("resident+pvu", dict(sched["sssp"], columns="plain"), sched["pagerank"]),
+            ("resident+pvu+packed", sched["sssp"], sched["pagerank"]),
+        ]
+        line["ablation"] = {}
+        for name, ks, kp in ladder:
+            a1, a2 = step(ks, kp)
+            line["ablation"][name] = {
+                "time_to_fixpoint_s": {"sssp": a1["time_ms"] / 1e3, "pagerank": a2["time_ms"] / 1e3},
+                "sweeps": {"sssp": a1["sweeps"], "pagerank": a2["sweeps"]},
+                "streamed_gb": {"sssp": a1["bytes_streamed"] / 1e9, "pagerank": a2["bytes_streamed"] / 1e9},
+                "edges_relaxed": {"sssp": a1["edges_relaxed"], "pagerank": a2["edges_relaxed"]},
+                "gteps": 2 * E / ((a1["time_ms"] + a2["time_ms"]) / 1e3) / 1e9}
     if not args.no_learned:
         from paper_1806_00762_b300 import train_sched
         params = train_sched.load()
