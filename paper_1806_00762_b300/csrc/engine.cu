@@ -681,11 +681,17 @@ __global__ void gate_kernel(RunState* rs, uint32_t pass, int check_prev, int idl
     else rs->cur.passes_skipped += 1;
 }
 
+// Vertices of the window to attempt, by in-degree class, in vertex order
+// within each block: warp w of a block takes vertices [v0 + 128w, +128) in
+// four rounds of 32; per class, ballots give each lane its place, one shared
+// exchange gives each warp its offset, one atomic per class and block
+// reserves the block's run of the list.
 template <int ALGO>
 __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a, uint32_t pass,
                                                       int predict) {
-    __shared__ unsigned ws[kNT / 32 + 1];
-    __shared__ unsigned s_base[kClasses];
+    constexpr int kWarps = kNT / 32;
+    __shared__ unsigned s_cnt[kWarps][kClasses + 2];
+    __shared__ unsigned s_off[kWarps][kClasses];
     const int par = pass & 1;
     RunState* rs = a.rs;
     if (!rs->pass_go[par]) return;
@@ -698,16 +704,17 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
     uint32_t thr = 0;
     if (strong) thr = ALGO == ALG_BFS ? rs->sweeps_done : min(rs->thr_prev, rs->thr_cur);
 
-    unsigned long long my_ent[kCompactRounds];
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t vw = cd.v_begin + (blockIdx.x - cd.block_begin) * kCompactTile + warp * 32 * kCompactRounds;
     int my_cls[kCompactRounds];
+    uint32_t my_p[kCompactRounds];
     unsigned n_att = 0, n_skip = 0;
-    const uint32_t v0 = cd.v_begin + (blockIdx.x - cd.block_begin) * kCompactTile;
 #pragma unroll
     for (int r = 0; r < kCompactRounds; ++r) {
         my_cls[r] = -1;
-        my_ent[r] = 0;
-        const uint32_t v = v0 + r * kNT + threadIdx.x;
-        if (v >= v0 && v < cd.v_end) {
+        my_p[r] = 0;
+        const uint32_t v = vw + r * 32 + lane;
+        if (v >= vw && v < cd.v_end) {
             const uint32_t p = find_page(a.vb, cd.first_page, cd.end_page, v);
             const PageLoc loc = a.loc[p];
             const uint32_t li = v - loc.vb;
@@ -731,31 +738,57 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
                               : deg <= a.cls_max[1] ? 1
                               : deg <= a.cls_max[2] ? 2
                               : deg <= a.cls_max[3] ? 3 : 4;
-                    my_ent[r] = ((unsigned long long)p << 32) | v;
+                    my_p[r] = p;
                 }
             }
         }
     }
+    unsigned m[kCompactRounds][kClasses];
+    unsigned cnt[kClasses];
 #pragma unroll
     for (int k = 0; k < kClasses; ++k) {
-        unsigned mine = 0;
+        cnt[k] = 0;
 #pragma unroll
-        for (int r = 0; r < kCompactRounds; ++r) mine += my_cls[r] == k;
-        unsigned tot, ex = block_excl_scan<kNT>(mine, ws, &tot);
-        if (tot == 0) continue;  // uniform: every thread sees the same total
-        if (threadIdx.x == 0) s_base[k] = atomicAdd(&rs->list_cnt[par][k], tot);
-        __syncthreads();
-        unsigned pos = s_base[k] + ex;
-#pragma unroll
-        for (int r = 0; r < kCompactRounds; ++r)
-            if (my_cls[r] == k) a.list[k][pos++] = my_ent[r];
+        for (int r = 0; r < kCompactRounds; ++r) {
+            m[r][k] = __ballot_sync(kFull, my_cls[r] == k);
+            cnt[k] += __popc(m[r][k]);
+        }
     }
-    unsigned tot_att, tot_skip;
-    block_excl_scan<kNT>(n_att, ws, &tot_att);
-    block_excl_scan<kNT>(n_skip, ws, &tot_skip);
-    if (threadIdx.x == 0) {
-        if (tot_att) atomicAdd(&rs->cur.attempted, (unsigned long long)tot_att);
-        if (tot_skip) atomicAdd(&rs->cur.skipped, (unsigned long long)tot_skip);
+    n_att = __reduce_add_sync(kFull, n_att);
+    n_skip = __reduce_add_sync(kFull, n_skip);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kClasses; ++k) s_cnt[warp][k] = cnt[k];
+        s_cnt[warp][kClasses] = n_att;
+        s_cnt[warp][kClasses + 1] = n_skip;
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses) {  // thread k: class k's run of the list for this block
+        const unsigned k = threadIdx.x;
+        unsigned tot = 0;
+        for (int w = 0; w < kWarps; ++w) tot += s_cnt[w][k];
+        unsigned base = tot ? atomicAdd(&rs->list_cnt[par][k], tot) : 0u;
+        for (int w = 0; w < kWarps; ++w) {
+            s_off[w][k] = base;
+            base += s_cnt[w][k];
+        }
+    } else if (threadIdx.x == 32) {
+        unsigned att = 0, sk = 0;
+        for (int w = 0; w < kWarps; ++w) { att += s_cnt[w][kClasses]; sk += s_cnt[w][kClasses + 1]; }
+        if (att) atomicAdd(&rs->cur.attempted, (unsigned long long)att);
+        if (sk) atomicAdd(&rs->cur.skipped, (unsigned long long)sk);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kClasses; ++k) {
+        unsigned pos = s_off[warp][k];
+#pragma unroll
+        for (int r = 0; r < kCompactRounds; ++r) {
+            if (my_cls[r] == k)
+                a.list[k][pos + __popc(m[r][k] & lanemask_lt())] =
+                    ((unsigned long long)my_p[r] << 32) | (vw + r * 32 + lane);
+            pos += __popc(m[r][k]);
+        }
     }
 }
 
