@@ -367,6 +367,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         }
         a.hints = hot_bytes > 0;
         a.hot = (uint32_t)std::min<uint64_t>(n, hot_bytes / 4);
+        // set-aside = the hot range (measured: a larger set-aside starves the
+        // normal lines -- 5/3 of 48 MB cost 8 % of PageRank's relax time)
         if (a.hints) l2_guard.reserve(g->device, (uint64_t)a.hot * 4);
     }
 
