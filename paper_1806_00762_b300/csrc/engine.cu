@@ -281,8 +281,9 @@ __device__ __forceinline__ void gather8(const AlgoArgs& a, const PageLoc& loc, u
 
 // Bit i (0..3) set: byte i of w ends a code.
 __device__ __forceinline__ uint32_t leb_ends4(uint32_t w) {
-    const uint32_t t = ~w & 0x80808080u;
-    return ((t >> 7) & 1u) | ((t >> 14) & 2u) | ((t >> 21) & 4u) | ((t >> 28) & 8u);
+    // the four flag bits (7, 15, 23, 31) gathered into bits 28..31 by one
+    // multiply: the other partial products land on distinct bits below 24
+    return ((~w & 0x80808080u) * 0x00204081u) >> 28;
 }
 
 // Bits of the 16 bytes at c that start a code of the range [B, Eb); pt = the
