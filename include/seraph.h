@@ -231,7 +231,8 @@ typedef struct seraph_params {
     void*    trace;             /* seraph_trace* to fill, or NULL             */
     uint32_t columns;           /* page form streamed: SERAPH_COLUMNS_AUTO
                                    (packed when the graph has it), _PLAIN (u32
-                                   source ids) or _PACKED (LEB128 gaps)      */
+                                   source ids), _PACKED (LEB128 gaps) or
+                                   _HYBRID (packed prefix of the pages)      */
     uint32_t pad1;
     uint64_t l2_hot_bytes;      /* L2 residency hint (not in the paper): the
                                    gathered values of vertices with internal
@@ -250,6 +251,9 @@ typedef struct seraph_params {
 #define SERAPH_COLUMNS_AUTO   0u
 #define SERAPH_COLUMNS_PLAIN  1u
 #define SERAPH_COLUMNS_PACKED 2u
+#define SERAPH_COLUMNS_HYBRID 3u  /* the first pages packed, the rest plain: the
+                                     fewest packed pages with which every chunk
+                                     stays resident in the ring (window 1)   */
 
 typedef struct seraph_stats {
     uint32_t sweeps;            /* sweeps run                                 */

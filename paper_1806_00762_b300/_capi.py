@@ -37,7 +37,7 @@ ORDERS = {"cyclic": ORDER_CYCLIC, "zigzag": ORDER_ZIGZAG}
 SYMMETRIZE = 1
 REORDER = 2
 COMPRESS = 4
-COLUMNS = {"auto": 0, "plain": 1, "packed": 2}
+COLUMNS = {"auto": 0, "plain": 1, "packed": 2, "hybrid": 3}
 NOALLOC_MAX_VERTICES = 1 << 20
 INF = 0xFFFFFFFF
 

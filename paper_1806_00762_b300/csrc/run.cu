@@ -42,6 +42,7 @@ struct Chunk {
     uint64_t w_begin, w_bytes;  // weight byte range (0 bytes if not streamed)
     uint64_t w_slot_off;        // weights start this far into the slot
     uint32_t v_begin, v_end;
+    bool packed;                // pages in the packed form (else plain)
 };
 
 // Evict-last lines live in the L2 set-aside for persisting accesses, which is
@@ -238,43 +239,62 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CUDA(cudaSetDevice(g->device));
 
     // ------------------------------------------------------------ chunking
-    SR_CHECK(P->columns <= SERAPH_COLUMNS_PACKED, SERAPH_EINVAL, "bad columns");
-    const bool packed = P->columns == SERAPH_COLUMNS_PACKED ||
-                        (P->columns == SERAPH_COLUMNS_AUTO && g->packed);
-    SR_CHECK(!packed || g->packed, SERAPH_EINVAL, "graph was built without SERAPH_COMPRESS");
-    // structure bytes of a page in the streamed form (plain u32 columns or packed gaps)
-    auto st_off = [&](const PageMeta& pm) { return packed ? pm.pk_off : pm.s_off; };
-    auto st_bytes = [&](const PageMeta& pm) { return packed ? pm.pk_bytes : pm.s_bytes; };
-    const uint8_t* h_struct = packed ? g->h_pack.p : g->h_struct.p;
+    SR_CHECK(P->columns <= SERAPH_COLUMNS_HYBRID, SERAPH_EINVAL, "bad columns");
+    const bool any_packed = P->columns != SERAPH_COLUMNS_PLAIN &&
+                            (P->columns != SERAPH_COLUMNS_AUTO || g->packed);
+    SR_CHECK(!any_packed || g->packed, SERAPH_EINVAL, "graph was built without SERAPH_COMPRESS");
+    const bool hybrid = P->columns == SERAPH_COLUMNS_HYBRID;
+    SR_CHECK(!hybrid || P->window == 1, SERAPH_EINVAL, "hybrid page forms need window = 1");
     const uint32_t W = P->window;
     const uint32_t R = P->slots ? P->slots : W + 1;
     SR_CHECK(R >= W + 1 && R <= 4096, SERAPH_EINVAL, "slots must be in [window+1, 4096]");
     const uint64_t slot_bytes = (P->budget_bytes / R) & ~255ull;
     SR_CHECK(slot_bytes >= 256, SERAPH_EBUDGET, "budget too small for the ring");
-    std::vector<Chunk> chunks;
-    {
+    // Pages [0, npk) stream packed, the rest plain (npk = 0 or P for one form).
+    // Chunks are runs of consecutive pages of one form that fit a slot.
+    auto make_chunks = [&](uint32_t npk, std::vector<Chunk>& out) {
+        out.clear();
         Chunk cur{};
         bool open = false;
         for (uint32_t p = 0; p < g->num_pages; ++p) {
             const PageMeta& pm = g->pages[p];
+            const bool pk = p < npk;
+            const uint64_t sb = pk ? pm.pk_bytes : pm.s_bytes;
             const uint64_t wb = use_w ? pm.w_bytes : 0;
-            SR_CHECK(align_up(st_bytes(pm), 256) + wb <= slot_bytes, SERAPH_EBUDGET,
-                     "page " + std::to_string(p) + " (" + std::to_string(st_bytes(pm) + wb) +
+            SR_CHECK(align_up(sb, 256) + wb <= slot_bytes, SERAPH_EBUDGET,
+                     "page " + std::to_string(p) + " (" + std::to_string(sb + wb) +
                          " B) does not fit a ring slot of " + std::to_string(slot_bytes) + " B");
-            if (open && align_up(cur.s_bytes + st_bytes(pm), 256) + cur.w_bytes + wb <= slot_bytes) {
+            if (open && cur.packed == pk && align_up(cur.s_bytes + sb, 256) + cur.w_bytes + wb <= slot_bytes) {
                 cur.end_page = p + 1;
-                cur.s_bytes += st_bytes(pm);
+                cur.s_bytes += sb;
                 cur.w_bytes += wb;
                 cur.v_end = (uint32_t)(pm.vb + pm.nv);
                 continue;
             }
-            if (open) chunks.push_back(cur);
-            cur = Chunk{p, p + 1, st_off(pm), st_bytes(pm), pm.w_off, wb, 0, (uint32_t)pm.vb,
-                        (uint32_t)(pm.vb + pm.nv)};
+            if (open) out.push_back(cur);
+            cur = Chunk{p, p + 1, pk ? pm.pk_off : pm.s_off, sb, pm.w_off, wb, 0, (uint32_t)pm.vb,
+                        (uint32_t)(pm.vb + pm.nv), pk};
             open = true;
         }
-        if (open) chunks.push_back(cur);
+        if (open) out.push_back(cur);
+    };
+    std::vector<Chunk> chunks;
+    uint32_t npk = any_packed ? g->num_pages : 0;
+    if (hybrid) {
+        // the fewest packed pages (the first pages hold the most-connected
+        // destinations when vertices are in out-degree order, and their gaps
+        // are short) with which every chunk stays resident in the ring
+        std::vector<Chunk> trial;
+        uint32_t lo = 0, hi = g->num_pages;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) / 2;
+            make_chunks(mid, trial);
+            if (trial.size() <= R) hi = mid; else lo = mid + 1;
+        }
+        npk = lo;
     }
+    make_chunks(npk, chunks);
+    const bool packed = npk > 0;  // some pages stream packed
     for (auto& c : chunks) c.w_slot_off = align_up(c.s_bytes, 256);
     const uint32_t C = (uint32_t)chunks.size();
     const bool resident = C <= R;
@@ -284,7 +304,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     std::vector<uint64_t> rel_soff(g->num_pages), rel_woff(g->num_pages), offb(g->num_pages);
     for (const Chunk& c : chunks)
         for (uint32_t p = c.first_page; p < c.end_page; ++p) {
-            rel_soff[p] = st_off(g->pages[p]) - c.s_begin;
+            rel_soff[p] = (c.packed ? g->pages[p].pk_off : g->pages[p].s_off) - c.s_begin;
             rel_woff[p] = c.w_slot_off + (g->pages[p].w_off - c.w_begin);
             offb[p] = g->pages[p].off_bytes;
         }
@@ -507,13 +527,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         const Chunk& ch = chunks[c];
         uint8_t* sb = ebuf.p + (uint64_t)slot * slot_bytes;
         if (prof) SR_CUDA(cudaEventRecord(pc_b[(load_seq + 1) % ring].e, xs.s));
-        SR_CUDA(cudaMemcpyAsync(sb, h_struct + ch.s_begin, ch.s_bytes, cudaMemcpyHostToDevice, xs.s));
+        SR_CUDA(cudaMemcpyAsync(sb, (ch.packed ? g->h_pack.p : g->h_struct.p) + ch.s_begin, ch.s_bytes,
+                                cudaMemcpyHostToDevice, xs.s));
         if (use_w && ch.w_bytes)
             SR_CUDA(cudaMemcpyAsync(sb + ch.w_slot_off, g->h_weight.p + ch.w_begin, ch.w_bytes,
                                     cudaMemcpyHostToDevice, xs.s));
         if (prof) SR_CUDA(cudaEventRecord(pc_e[(load_seq + 1) % ring].e, xs.s));
         launch_set_locs(loc.p, g->d_vb.p, ch.first_page, ch.end_page, d_rel_soff.p, d_rel_woff.p,
-                        d_offb.p, sb, use_w ? sb : nullptr, packed, rs.p, ++load_seq, xs.s);
+                        d_offb.p, sb, use_w ? sb : nullptr, ch.packed, rs.p, ++load_seq, xs.s);
         ++launches;
         SR_CUDA(cudaEventRecord(copy_done[c].e, xs.s));
         slot_of[c] = slot;
@@ -652,7 +673,11 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
                         j < 16 ? rec_row : nullptr, cs.s);
             launch_compact(algo, wd, a, pass, pred_now ? 1 : 0, cs.s);
             if (prof) SR_CUDA(cudaEventRecord(pr_b[(t % ring) * max_passes + j].e, cs.s));
-            launch_relax(algo, P->kahan, a, pass, (uint32_t)t, relax_grid, cs.s);
+            {
+                AlgoArgs ap = a;
+                ap.packed = chunks[win[0]].packed;  // windows hold one form (hybrid needs W = 1)
+                launch_relax(algo, P->kahan, ap, pass, (uint32_t)t, relax_grid, cs.s);
+            }
             if (prof) SR_CUDA(cudaEventRecord(pr_e[(t % ring) * max_passes + j].e, cs.s));
             launches += 3;
             S.relax_launches += 1;

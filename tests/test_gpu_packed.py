@@ -150,3 +150,35 @@ def test_five_byte_codes_and_hub_lists():
     d, _ = seraph.run(g, "sssp", source=s, window=2, columns="packed",
                       budget_bytes=packed_budget(g, 3))
     assert np.array_equal(d, oracle.sssp(og, s))
+
+
+@pytest.mark.parametrize("algo", ["sssp", "bfs", "cc", "pagerank"])
+def test_hybrid_forms_keep_every_chunk_resident(r13p, algo):
+    """columns="hybrid" packs the fewest leading pages with which every chunk
+    fits the ring: with a budget between the plain and the packed totals the
+    plain form must stream every sweep, the hybrid one stays resident, and both
+    give the oracle's results."""
+    g = r13p["gs"] if algo == "cc" else r13p["gr"]
+    i = g.info()
+    use_w = algo == "sssp"
+    wb = i["weight_bytes"] if use_w else 0
+    budget = int(((i["struct_bytes"] + i["packed_bytes"]) / 2 + wb) * 1.25)
+    kw = dict(source=5, window=1, slots=12, budget_bytes=budget)
+    if algo == "pagerank":
+        kw["pvu"] = "weak"
+    h, sh = seraph.run(g, algo, columns="hybrid", **kw)
+    p, sp = seraph.run(g, algo, columns="plain", **kw)
+    assert sh["resident"] == 1 and sp["resident"] == 0
+    assert sh["bytes_streamed"] < sp["bytes_streamed"]
+    for got in (h, p):
+        if algo == "pagerank":
+            l1, rel = pr_errors(got, r13p["pr"])
+            assert l1 <= PR_L1 and rel <= PR_REL
+        else:
+            assert np.array_equal(got, r13p[algo])
+
+
+def test_hybrid_needs_window_one(r13p):
+    with pytest.raises(SeraphError, match="EINVAL"):
+        seraph.run(r13p["gr"], "bfs", columns="hybrid", window=2,
+                   budget_bytes=packed_budget(r13p["gr"], 3, False))
