@@ -39,8 +39,8 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-fixpoint and effective GTEPS, RMAT-28 streamed; learned vs fixed sched"
 
 
-DEFAULT_SSSP = "order=cyclic,window=1,slots=32,pvu=strong,verify=0,columns=packed"
-DEFAULT_PAGERANK = "order=zigzag,window=1,slots=32,pvu=weak,columns=plain"
+DEFAULT_SSSP = "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid"
+DEFAULT_PAGERANK = "order=zigzag,window=1,slots=12,pvu=weak,columns=hybrid"
 
 
 def parse():
@@ -530,8 +530,11 @@ def main():
              dict(order="cyclic", window=4, slots=5, pvu="off", columns="plain")),
             ("psi+pvu", dict(order="cyclic", window=4, slots=5, pvu="strong", columns="plain"),
              dict(order="cyclic", window=4, slots=5, pvu="weak", columns="plain")),
-            ("resident+pvu", dict(sched["sssp"], columns="plain"), sched["pagerank"]),
-            ("resident+pvu+packed", sched["sssp"], sched["pagerank"]),
+            ("resident+pvu", dict(sched["sssp"], slots=32, columns="plain"),
+             dict(sched["pagerank"], slots=32, columns="plain")),
+            ("resident+pvu+packed", dict(sched["sssp"], slots=32, columns="packed"),
+             dict(sched["pagerank"], slots=32, columns="plain")),
+            ("resident+pvu+hybrid", sched["sssp"], sched["pagerank"]),
         ]
         line["ablation"] = {}
         for name, ks, kp in ladder:
