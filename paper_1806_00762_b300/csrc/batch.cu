@@ -588,8 +588,18 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
                           (uint32_t)g->n, g->adj.wbytes};
     }
     std::vector<BQuery> qh(nq);
+    // every per-query array comes out of one allocation (one cudaMalloc per
+    // call instead of several per query), each array 128-byte aligned
+    auto words = [](uint64_t n) { return (n + 31) & ~31ull; };
+    uint64_t pool_words = 0;
+    for (const QSpec& Q : qs) {
+        const uint64_t n = graphs[Q.graph]->n;
+        pool_words += words(n) * ((Q.out ? 0 : 1) + 3 + (Q.algo == SERAPH_SSSP ? 3 : 0));
+    }
     hold->clear();
-    hold->reserve(7 * (size_t)nq);
+    hold->emplace_back(std::max<uint64_t>(pool_words, 1));
+    uint32_t* pool = hold->back().p;
+    auto carve = [&](uint64_t n) { uint32_t* p = pool; pool += words(n); return p; };
     uint64_t tiles = 0;
     uint32_t max_n = 1;
     for (uint32_t q = 0; q < nq; ++q) {
@@ -598,20 +608,15 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
         max_n = std::max<uint32_t>(max_n, (uint32_t)n);
         BQuery b{};
         b.graph = Q.graph; b.algo = Q.algo; b.source = Q.source; b.mapping = Q.mapping; b.tile = Q.tile;
-        if (Q.out) {
-            b.dist = Q.out;
-        } else {
-            hold->emplace_back(n);
-            b.dist = hold->back().p;
-        }
-        hold->emplace_back(n); b.stamp = hold->back().p;
-        hold->emplace_back(n); b.front[0] = hold->back().p;
-        hold->emplace_back(n); b.front[1] = hold->back().p;
+        b.dist = Q.out ? Q.out : carve(n);
+        b.stamp = carve(n);
+        b.front[0] = carve(n);
+        b.front[1] = carve(n);
         b.delta = Q.delta ? Q.delta : 1u;
         if (Q.algo == SERAPH_SSSP) {  // far piles and their per-epoch stamps
-            hold->emplace_back(n); b.far[0] = hold->back().p;
-            hold->emplace_back(n); b.far[1] = hold->back().p;
-            hold->emplace_back(n); b.fstamp = hold->back().p;
+            b.far[0] = carve(n);
+            b.far[1] = carve(n);
+            b.fstamp = carve(n);
         }
         qh[q] = b;
         tiles += (n + Q.tile - 1) / Q.tile + graphs[Q.graph]->adj.E / kPartEdges + 1;
@@ -769,8 +774,8 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
     const Outcome o = launch_batch(graphs, qs, P->use_graph != 0, P->replays, P->timeout_ms, s.s, &dist, &hold);
     if (out_mem == SERAPH_MEM_HOST)
         for (uint32_t q = 0; q < nq; ++q)
-            SR_CUDA(cudaMemcpy(qin[q].out, dist[q], graphs[qin[q].graph]->n * sizeof(uint32_t),
-                               cudaMemcpyDeviceToHost));
+            SR_CUDA(cudaMemcpyAsync(qin[q].out, dist[q], graphs[qin[q].graph]->n * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, s.s));
     SR_CUDA(cudaStreamSynchronize(s.s));
     S.time_ms = o.ms;
     S.edges = o.edges;
