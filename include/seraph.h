@@ -161,6 +161,12 @@ int  seraph_graph_export_perm(const seraph_graph* g, uint32_t* perm);
  * destination's bytes, data[packed_data_bytes].  Either may be NULL. */
 int  seraph_graph_export_packed(const seraph_graph* g, uint64_t* boff, uint8_t* data);
 
+/* A run keeps its device buffers (edge ring, vertex arrays, lists) with the
+ * graph for the next run, so repeated runs allocate nothing; this returns
+ * them to the device (seraph_graph_free does too).  Must not overlap a run on
+ * the same graph. */
+int  seraph_graph_release_buffers(seraph_graph* g);
+
 void seraph_graph_free(seraph_graph* g);
 
 /*

@@ -125,6 +125,10 @@ class Graph:
         C.check(C.lib().seraph_graph_export_packed(self._h, boff.ctypes.data, data.ctypes.data))
         return boff, data[:i["packed_data_bytes"]]
 
+    def release_buffers(self) -> None:
+        """Give back the device buffers that runs keep with the graph."""
+        C.check(C.lib().seraph_graph_release_buffers(self._h))
+
     def perm(self) -> np.ndarray:
         """Internal vertex order: perm[i] = the caller's id of internal vertex i."""
         p = np.empty(self.info()["n"], dtype=np.uint32)

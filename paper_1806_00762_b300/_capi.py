@@ -114,6 +114,7 @@ PROTOTYPES = {
     "seraph_graph_export_csc": (ctypes.c_int, [vp, vp, vp, vp, vp]),
     "seraph_graph_export_perm": (ctypes.c_int, [vp, vp]),
     "seraph_graph_export_packed": (ctypes.c_int, [vp, vp, vp]),
+    "seraph_graph_release_buffers": (ctypes.c_int, [vp]),
     "seraph_graph_free": (None, [vp]),
     "seraph_params_default": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int]),
     "seraph_run": (ctypes.c_int, [vp, ctypes.POINTER(Params), vp, ctypes.c_int,

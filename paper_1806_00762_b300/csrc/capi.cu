@@ -176,6 +176,16 @@ int seraph_graph_export_packed(const seraph_graph* g, uint64_t* boff, uint8_t* d
     });
 }
 
+int seraph_graph_release_buffers(seraph_graph* g) {
+    return guarded([&] {
+        SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
+        std::lock_guard<std::mutex> lk(g->ws.m);
+        SR_CUDA(cudaSetDevice(g->device));
+        g->ws.release();
+        return SERAPH_OK;
+    });
+}
+
 void seraph_graph_free(seraph_graph* g) {
     if (!g) return;
     try {

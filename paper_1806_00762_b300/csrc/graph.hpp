@@ -2,9 +2,26 @@
 // plus the vertex-side arrays that stay resident on the device.
 #pragma once
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
+
+// Device buffers of a run kept with the graph for the next run (a serving
+// loop then allocates nothing after its first call).  Held by one run at a
+// time; a concurrent run on the same graph allocates its own.
+struct RunWorkspace {
+    std::mutex m;
+    seraph::DevBuf<uint8_t> ebuf;                // the edge ring
+    seraph::DevBuf<unsigned long long> lists;    // compaction lists
+    seraph::DevBuf<uint32_t> val, out;           // values; caller-order output staging
+    seraph::DevBuf<float> x, contrib, x_next, x_prev, inv_out;
+    seraph::DevBuf<uint8_t> state;
+    void release() {
+        ebuf.release(); lists.release(); val.release(); out.release(); x.release();
+        contrib.release(); x_next.release(); x_prev.release(); inv_out.release(); state.release();
+    }
+};
 
 // Static per-page description.  A page is a contiguous destination range
 // [vb, vb+nv) with all of its in-edges.  In the pinned structure region it is
@@ -50,6 +67,7 @@ struct seraph_graph {
     bool packed = false;               // built with SERAPH_COMPRESS
     seraph::PinnedBuf h_pack;          // all packed page structures, in page order
     seraph::DevBuf<uint8_t> d_pack_tmp; // gap streams while the graph is built
+    RunWorkspace ws;                   // buffers kept between runs
     bool reordered = false;            // built with SERAPH_REORDER
     seraph::DevBuf<uint32_t> d_perm;   // internal id -> caller's id (reordered only)
     seraph::DevBuf<uint32_t> d_inv;    // caller's id -> internal id (reordered only)

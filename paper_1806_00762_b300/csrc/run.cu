@@ -325,13 +325,41 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     Stream cs, xs;
     cs.use(P->stream);
     xs.create();
-    DevBuf<uint8_t> ebuf(slot_bytes * nslots);
+    DevBuf<uint8_t> ebuf;
+    DevBuf<unsigned long long> lists;
+    DevBuf<uint32_t> val, caller_order;
+    DevBuf<float> x, contrib, x_next, x_prev, inv_out;
+    DevBuf<uint8_t> state;
+    // borrow the graph's kept buffers for this run (given back on every exit)
+    struct Lease {
+        RunWorkspace* ws = nullptr;
+        DevBuf<uint8_t>* ebuf; DevBuf<unsigned long long>* lists; DevBuf<uint32_t>* val;
+        DevBuf<uint32_t>* out; DevBuf<float>* f[5]; DevBuf<uint8_t>* state;
+        ~Lease() {
+            if (!ws) return;
+            ws->ebuf = std::move(*ebuf); ws->lists = std::move(*lists); ws->val = std::move(*val);
+            ws->out = std::move(*out); ws->x = std::move(*f[0]); ws->contrib = std::move(*f[1]);
+            ws->x_next = std::move(*f[2]); ws->x_prev = std::move(*f[3]);
+            ws->inv_out = std::move(*f[4]); ws->state = std::move(*state);
+            ws->m.unlock();
+        }
+    } lease{nullptr, &ebuf, &lists, &val, &caller_order, {&x, &contrib, &x_next, &x_prev, &inv_out}, &state};
+    if (g->ws.m.try_lock()) {
+        RunWorkspace& w = g->ws;
+        ebuf = std::move(w.ebuf); lists = std::move(w.lists); val = std::move(w.val);
+        caller_order = std::move(w.out); x = std::move(w.x); contrib = std::move(w.contrib);
+        x_next = std::move(w.x_next); x_prev = std::move(w.x_prev); inv_out = std::move(w.inv_out);
+        state = std::move(w.state);
+        lease.ws = &w;
+    }
+    auto ensure = [](auto& buf, size_t count) { if (buf.n < count) buf.alloc(count); };
+    ensure(ebuf, slot_bytes * nslots);
     DevBuf<PageLoc> loc(g->num_pages);
     DevBuf<uint64_t> d_rel_soff(g->num_pages), d_rel_woff(g->num_pages), d_offb(g->num_pages);
     SR_CUDA(cudaMemcpyAsync(d_rel_soff.p, rel_soff.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
     SR_CUDA(cudaMemcpyAsync(d_rel_woff.p, rel_woff.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
     SR_CUDA(cudaMemcpyAsync(d_offb.p, offb.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
-    DevBuf<unsigned long long> lists((uint64_t)kClasses * max_win_v);
+    ensure(lists, (uint64_t)kClasses * max_win_v);
     DevBuf<RunState> rs(1);
     DevBuf<SweepReport> d_rep(1);
     DevBuf<unsigned> d_steps(ring);
@@ -339,26 +367,23 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     PinnedBuf h_rep, h_steps;
     h_rep.alloc(sizeof(SweepReport));
     h_steps.alloc(ring * sizeof(unsigned));
-    DevBuf<uint32_t> val;
-    DevBuf<float> x, contrib, x_next, x_prev, inv_out;
-    DevBuf<uint8_t> state;
     const int nparts = device_sms() * 4;
     DevBuf<double> partial;
     if (is_pr) {
-        x.alloc(n); contrib.alloc(n); x_next.alloc(n); x_prev.alloc(n); inv_out.alloc(n);
+        ensure(x, n); ensure(contrib, n); ensure(x_next, n); ensure(x_prev, n); ensure(inv_out, n);
         partial.alloc(2 * nparts);
     } else {
-        val.alloc(n);
+        ensure(val, n);
     }
-    if (P->pvu == SERAPH_PVU_WEAK) state.alloc(n);
+    if (P->pvu == SERAPH_PVU_WEAK) ensure(state, n);
 
     AlgoArgs a{};
-    a.val = val.p;
-    a.x = x.p;
-    a.contrib = contrib.p;
-    a.x_next = x_next.p;
-    a.inv_out = inv_out.p;
-    a.state = state.p;
+    a.val = is_pr ? nullptr : val.p;  // (borrowed buffers of other algorithms stay unused)
+    a.x = is_pr ? x.p : nullptr;
+    a.contrib = is_pr ? contrib.p : nullptr;
+    a.x_next = is_pr ? x_next.p : nullptr;
+    a.inv_out = is_pr ? inv_out.p : nullptr;
+    a.state = P->pvu == SERAPH_PVU_WEAK ? state.p : nullptr;
     a.rs = rs.p;
     a.loc = loc.p;
     a.vb = g->d_vb.p;
@@ -819,11 +844,10 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
 
     // ------------------------------------------------------------- output
     const void* src = is_pr ? (const void*)x.p : (const void*)val.p;
-    DevBuf<uint32_t> caller_order;
     if (out && g->reordered) {  // back to the caller's vertex ids
         uint32_t* dst = out_mem == SERAPH_MEM_DEVICE ? (uint32_t*)out : nullptr;
         if (!dst) {
-            caller_order.alloc(n);
+            ensure(caller_order, n);
             dst = caller_order.p;
         }
         launch_unpermute((const uint32_t*)src, g->d_inv.p, n, dst, cs.s);

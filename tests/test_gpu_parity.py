@@ -331,3 +331,18 @@ def test_output_to_device_tensor(r16):
     out = torch.empty(r16["n"], dtype=torch.int32, device="cuda")
     seraph.run(r16["g"], "sssp", out=out, **cfg1(r16["g"]))
     assert np.array_equal(out.cpu().numpy().view(np.uint32), r16["sssp"])
+
+
+def test_runs_reuse_and_release_kept_buffers(r16):
+    """Consecutive runs on one graph borrow the buffers the previous run kept
+    (different algorithms and ring sizes in turn); releasing them between runs
+    changes nothing in the results."""
+    g = r16["g"]
+    for k in range(2):
+        d, _ = seraph.run(g, "sssp", **cfg1(g))
+        x, _ = seraph.run(g, "pagerank", window=1, slots=3, budget_bytes=budget(g, 2, 1.0, False))
+        b, _ = seraph.run(g, "bfs", window=2, pvu="weak", budget_bytes=budget(g, 2, 1.0, False))
+        assert np.array_equal(d, r16["sssp"]) and np.array_equal(b, r16["bfs"])
+        assert pr_errors(x, r16["pr"])[0] <= PR_L1
+        if k == 0:
+            g.release_buffers()
