@@ -422,6 +422,12 @@ typedef struct seraph_batch_params {
                                    rest wait in a far pile until the split
                                    rises by delta; BFS ignores it            */
     void*    stream;            /* cudaStream_t, NULL = own                   */
+    uint32_t bfs_pull_div;      /* BFS direction switch (Beamer et al.): a
+                                   round whose frontier exceeds n / div runs
+                                   bottom-up -- every unvisited vertex looks
+                                   for a parent among its in-neighbours --
+                                   instead of pushing (0 = 5; 1 = never)     */
+    uint32_t reserved2;
 } seraph_batch_params;
 
 typedef struct seraph_batch_stats {

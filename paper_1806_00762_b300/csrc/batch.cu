@@ -39,6 +39,8 @@ struct BGraphDev {
     const uint32_t* col;
     const uint8_t* w;
     uint32_t n, wbytes;
+    const uint64_t* in_off;   // in-edge rows (bottom-up BFS)
+    const uint32_t* in_col;
 };
 
 // SSSP queries order their work near-far: improved vertices whose distance is
@@ -49,7 +51,7 @@ struct BGraphDev {
 // BFS queries keep split = infinity (plain level-synchronous push).
 struct BQuery {
     uint32_t graph, algo, source, mapping, tile;
-    uint32_t round, cur_n, next_n, tiles_total, tiles_done, done, pad;
+    uint32_t round, cur_n, next_n, tiles_total, tiles_done, done, pull_min;
     uint32_t split, delta, phase, fsel, epoch, far_min, far_n[2];
     uint32_t* dist;
     uint32_t* stamp;
@@ -58,7 +60,9 @@ struct BQuery {
     uint32_t* fstamp;
 };
 
-constexpr uint32_t kPhaseNear = 0, kPhaseFilter = 1;
+constexpr uint32_t kPhaseNear = 0, kPhaseFilter = 1, kPhasePull = 2;
+constexpr uint32_t kPullTile = 1024;  // vertices per bottom-up task
+constexpr uint32_t kDefaultPullDiv = 5;  // pull when the frontier exceeds n / 5 (measured best of 1..100)
 constexpr uint32_t kDefaultDelta = 64;  // near-far bucket width when the caller gives none
 
 struct BGlobal {
@@ -155,7 +159,7 @@ __device__ __forceinline__ BQuery load_query(const BQuery* p) {
     const volatile BQuery* v = p;
     Q.graph = v->graph; Q.algo = v->algo; Q.source = v->source; Q.mapping = v->mapping;
     Q.tile = v->tile; Q.round = v->round; Q.cur_n = v->cur_n; Q.next_n = 0;
-    Q.tiles_total = 0; Q.tiles_done = 0; Q.done = 0; Q.pad = 0;
+    Q.tiles_total = 0; Q.tiles_done = 0; Q.done = 0; Q.pull_min = v->pull_min;
     Q.split = v->split; Q.delta = v->delta; Q.phase = v->phase; Q.fsel = v->fsel;
     Q.epoch = v->epoch; Q.far_min = 0; Q.far_n[0] = Q.far_n[1] = 0;
     Q.dist = v->dist; Q.stamp = v->stamp; Q.front[0] = v->front[0]; Q.front[1] = v->front[1];
@@ -281,6 +285,29 @@ __device__ bool publish(TaskSlot* ring, unsigned long long mask, unsigned long l
     return ok;
 }
 
+// A bottom-up BFS task: vertices [t0, t0 + cnt) of the graph.  Each unvisited
+// vertex scans its in-neighbours for one in the current frontier (level =
+// round) and stops at the first; only this thread writes its level, so no
+// atomics.  Found vertices form the next frontier.  Returns in-edges read.
+__device__ unsigned long long pull_tile(BQuery* qs, uint32_t q, const BQuery& Q,
+                                        const BGraphDev& G, uint32_t t0, uint32_t cnt) {
+    unsigned long long edges = 0;
+    for (uint32_t base = 0; base < cnt; base += kNT) {
+        const uint32_t v = t0 + base + threadIdx.x;
+        bool found = false;
+        if (base + threadIdx.x < cnt && __ldcg(Q.dist + v) == SERAPH_INF) {
+            const uint64_t b = G.in_off[v], e = G.in_off[v + 1];
+            for (uint64_t k = b; k < e; ++k) {
+                ++edges;
+                if (__ldcg(Q.dist + G.in_col[k]) == Q.round) { found = true; break; }
+            }
+            if (found) Q.dist[v] = Q.round + 1;
+        }
+        append(Q.front[(Q.round + 1) & 1], &qs[q].next_n, found, v);
+    }
+    return edges;
+}
+
 // One task: tile `tile` of query q's current frontier.  Returns edges relaxed.
 // Frontier entries and distances are mutable across rounds: read via L2.
 __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, uint32_t q,
@@ -295,6 +322,10 @@ __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, 
     if (Q.phase == kPhaseFilter) {
         filter_tile(qs, q, Q, t0, cnt);
         return 0;
+    }
+    if (Q.phase == kPhasePull) {
+        const uint32_t p0 = tile * kPullTile;
+        return pull_tile(qs, q, Q, G, p0, min(kPullTile, G.n - p0));
     }
     if (Q.mapping == SERAPH_MAP_THREAD) {
         for (uint32_t base = 0; base < cnt; base += kNT) {  // warps stay converged for the ballot
@@ -461,6 +492,7 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
                     Q->phase = kPhaseNear;
                     exact_min = true;
                 }
+                if (Q->phase == kPhasePull) Q->phase = kPhaseNear;
                 uint32_t nn = Q->next_n;
                 if (nn == 0 && Q->far_n[Q->fsel] > 0) {  // near frontier dry: filter the far pile
                     const uint32_t fs = Q->fsel;
@@ -474,12 +506,19 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
                     Q->epoch = Q->epoch + 1;
                     Q->phase = kPhaseFilter;
                 }
+                uint32_t tiles = (nn + Q->tile - 1) / Q->tile;
+                if (Q->algo == SERAPH_BFS && Q->phase == kPhaseNear && nn > Q->pull_min) {
+                    // a large frontier: the next round pulls over all vertices
+                    const uint32_t n = graphs[Q->graph].n;
+                    Q->phase = kPhasePull;
+                    tiles = (n + kPullTile - 1) / kPullTile;
+                }
                 Q->round = Q->round + 1;
                 atomicMax(&gl->max_round, Q->round);
                 Q->cur_n = nn;
                 Q->next_n = 0;
                 Q->tiles_done = 0;
-                Q->tiles_total = (nn + Q->tile - 1) / Q->tile;
+                Q->tiles_total = tiles;
                 s_count = Q->tiles_total;
                 if (nn == 0) {
                     Q->done = 1;
@@ -553,6 +592,7 @@ struct QSpec {
     uint32_t graph, algo, source, mapping, tile;
     uint32_t* out;  // device buffer for the distances, or null
     uint32_t delta; // near-far bucket width (SSSP)
+    uint32_t pull_div;  // BFS: pull when the frontier exceeds n / pull_div
 };
 
 struct Outcome {
@@ -585,7 +625,7 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
     for (size_t i = 0; i < graphs.size(); ++i) {
         const seraph_bgraph* g = graphs[i];
         gd[i] = BGraphDev{g->adj.off.p, g->adj.col.p, g->weighted ? g->adj.wptr() : nullptr,
-                          (uint32_t)g->n, g->adj.wbytes};
+                          (uint32_t)g->n, g->adj.wbytes, g->in_adj.off.p, g->in_adj.col.p};
     }
     std::vector<BQuery> qh(nq);
     // every per-query array comes out of one allocation (one cudaMalloc per
@@ -613,6 +653,7 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
         b.front[0] = carve(n);
         b.front[1] = carve(n);
         b.delta = Q.delta ? Q.delta : 1u;
+        b.pull_min = (uint32_t)(n / (Q.pull_div ? Q.pull_div : 1u));
         if (Q.algo == SERAPH_SSSP) {  // far piles and their per-epoch stamps
             b.far[0] = carve(n);
             b.far[1] = carve(n);
@@ -704,6 +745,8 @@ void bgraph_build(seraph_bgraph* g, uint64_t n, uint64_t m, const uint32_t* src,
     g->weighted = w != nullptr;
     // rows = sources: the sorted adjacency of the swapped edge list
     sorted_adjacency(n, m, dst, src, w, mem, false, s, g->adj);
+    // rows = destinations, for BFS rounds that pull from the frontier
+    sorted_adjacency(n, m, src, dst, nullptr, mem, false, s, g->in_adj);
 }
 
 int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* qin, uint32_t nq,
@@ -713,6 +756,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
     SR_CHECK(P->mapping >= SERAPH_MAP_AUTO && P->mapping <= SERAPH_MAP_CTA, SERAPH_EINVAL, "bad mapping");
     SR_CHECK(P->tile == 0 || (P->tile <= (1u << 20)), SERAPH_EINVAL, "bad tile");
     const uint32_t delta = P->delta ? P->delta : kDefaultDelta;
+    const uint32_t pull_div = P->bfs_pull_div ? P->bfs_pull_div : kDefaultPullDiv;
     std::vector<seraph_bgraph*> graphs(graphs_in, graphs_in + ng);
     for (auto* g : graphs) SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
     SR_CUDA(cudaSetDevice(graphs[0]->device));
@@ -737,7 +781,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
         std::vector<seraph_bgraph*> one{graphs[gi]};
         for (uint32_t q = 0; q < nq; ++q)
             if (qin[q].graph == gi)
-                sub.push_back(QSpec{0, (uint32_t)qin[q].algo, qin[q].source, 0, 0, nullptr, delta});
+                sub.push_back(QSpec{0, (uint32_t)qin[q].algo, qin[q].source, 0, 0, nullptr, delta, pull_div});
         float best = 1e30f;
         uint32_t bm = SERAPH_MAP_CTA, bt = 256;
         if (!sub.empty()) {
@@ -767,7 +811,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
         uint32_t tile = gtile[Q.graph];
         if (gmap[Q.graph] == SERAPH_MAP_CTA) tile = std::min<uint32_t>(tile, kMaxCtaTile);
         qs[q] = QSpec{Q.graph, algo, Q.source, gmap[Q.graph], tile,
-                      out_mem == SERAPH_MEM_DEVICE ? Q.out : nullptr, delta};
+                      out_mem == SERAPH_MEM_DEVICE ? Q.out : nullptr, delta, pull_div};
     }
     std::vector<uint32_t*> dist(nq);
     std::vector<DevBuf<uint32_t>> hold;

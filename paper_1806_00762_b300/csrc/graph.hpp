@@ -108,6 +108,7 @@ struct seraph_bgraph {
     uint64_t n = 0, m_raw = 0;
     bool weighted = false;
     seraph::Adjacency adj;        // rows = sources
+    seraph::Adjacency in_adj;     // rows = destinations (bottom-up BFS rounds), no weights
     int tuned_mapping = 0;        // 0: not tuned yet
     uint32_t tuned_tile = 0;
 };

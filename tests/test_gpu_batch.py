@@ -61,6 +61,19 @@ def test_near_far_bucket_widths(work, delta, mapping):
         assert np.array_equal(o, r)
 
 
+@pytest.mark.parametrize("pull_div", [1, 2, 20, 0xFFFFFFFF])
+@pytest.mark.parametrize("mapping", ["thread", "cta"])
+def test_bfs_direction_switch(work, pull_div, mapping):
+    """BFS rounds whose frontier exceeds n / pull_div run bottom-up (every
+    unvisited vertex looks for a parent in the frontier): never (1), on large
+    frontiers (2, 20) or after the first round always (2^32-1) -- the levels
+    stay exact, and SSSP queries in the same batch are unaffected."""
+    graphs, queries, refs = work
+    outs, _ = seraph.batch_run(graphs, queries, mapping=mapping, tile=64, bfs_pull_div=pull_div)
+    for o, r in zip(outs, refs):
+        assert np.array_equal(o, r)
+
+
 def test_autotune_result_is_cached_and_device_outputs(work):
     import torch
     graphs, queries, refs = work
