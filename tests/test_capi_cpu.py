@@ -51,7 +51,10 @@ int main(void) {{
 
 
 @pytest.mark.parametrize("name,cls", [("seraph_params", C.Params), ("seraph_stats", C.Stats),
-                                      ("seraph_graph_info", C.GraphInfo)])
+                                      ("seraph_graph_info", C.GraphInfo),
+                                      ("seraph_batch_params", C.BatchParams),
+                                      ("seraph_batch_stats", C.BatchStats),
+                                      ("seraph_query", C.Query), ("seraph_trace", C.Trace)])
 def test_struct_layout_matches_header(name, cls):
     fields = [f for f, _ in cls._fields_ if not f.startswith("pad")]
     got = _c_layout(name, fields)
