@@ -1,7 +1,7 @@
 """Train the learned scheduler on traces of the fixed pipeline.
 
 Traces come from SSSP, BFS and PageRank runs on seeded R-MAT graphs built as
-the benchmark builds them (out-degree order, packed and plain pages), at scale
+the benchmark builds them (out-degree order, hybrid pages), at scale
 24 with small ring slots and at scale 28 with the benchmark's ring, each step
 running up to 16 local passes so that the gain of every extra pass is seen.
 Targets (seraph_sched_targets): k = fewest passes holding 95 % of a step's
@@ -47,9 +47,9 @@ def collect(seraph, torch, g, budget, slots, runs):
         tr = seraph.TraceBuffer(500_000)
         out = torch.empty(n, dtype=torch.float32 if algo == "pagerank" else torch.int32,
                           device="cuda")
-        # the benchmark's page forms: SSSP/BFS stream packed columns, PageRank plain ones
+        # the benchmark's page form: hybrid (leading pages packed, the rest plain)
         seraph.run(g, algo, out=out, source=source, window=1, slots=slots, passes=16, trace=tr,
-                   budget_bytes=budget, columns="plain" if algo == "pagerank" else "packed")
+                   budget_bytes=budget, columns="hybrid")
         f, _, _ = tr.rows()
         k, p = tr.targets(0.95)
         xs.append(f.copy())
@@ -86,7 +86,7 @@ def main():
             x, k, p = collect(seraph, torch, g, 2 << 30, 64, runs)
         else:
             g = _graph(seraph, synth, torch, scale, 512)
-            x, k, p = collect(seraph, torch, g, 16 << 30, 32, [("sssp", 0), ("pagerank", 0)])
+            x, k, p = collect(seraph, torch, g, 16 << 30, 16, [("sssp", 0), ("pagerank", 0)])
         xs += x
         ks += k
         ps += p
