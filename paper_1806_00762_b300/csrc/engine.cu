@@ -532,8 +532,10 @@ __device__ __forceinline__ void vertex_thread(const AlgoArgs& a, unsigned long l
     if constexpr (PK) {
         edges_packed_serial<ALGO, KAHAN, WB>(a, loc, li, b, macc, sacc);
     } else {
-        for (uint32_t idx = b & ~3u; idx < e; idx += 8)
+        for (uint32_t idx = b & ~3u; idx < e; idx += 8) {
             gather8<ALGO, KAHAN, WB>(a, loc, b, e, idx, idx + 4, macc, sacc);
+            if (ALGO == ALG_BFS && macc.best <= a.bfs_lb) break;  // no smaller level exists
+        }
     }
     if (ALGO == ALG_PR) finish_pr(a, v, sacc.s - sacc.c, base, e - b, L, own);
     else finish_min<ALGO>(a, v, macc, e - b, L, own);
@@ -546,8 +548,10 @@ template <int ALGO, bool KAHAN, int WB>
 __device__ __forceinline__ void edges_strided(const AlgoArgs& a, const PageLoc& loc, uint32_t b,
                                               uint32_t e, uint32_t t, uint32_t G, MinAcc& macc,
                                               SumAcc& sacc) {
-    for (uint32_t idx = (b & ~3u) + 4 * t; idx < e; idx += 8 * G)
+    for (uint32_t idx = (b & ~3u) + 4 * t; idx < e; idx += 8 * G) {
         gather8<ALGO, KAHAN, WB>(a, loc, b, e, idx, idx + 4 * G, macc, sacc);
+        if (ALGO == ALG_BFS && macc.best <= a.bfs_lb) break;  // this lane can find nothing smaller
+    }
 }
 
 // One vertex per group of G lanes (G = 4, 8 or 32), 32/G vertices per warp

@@ -92,6 +92,8 @@ struct AlgoArgs {
     uint8_t packed;           // pages hold LEB128 gap streams (SERAPH_COMPRESS)
     uint32_t hot;             // gathers of vertices < hot: L2 evict-last
     uint32_t n;               // vertices
+    uint32_t bfs_lb;          // BFS: no attempted vertex can reach a level below this, so a
+                              // lane that finds it stops scanning (early-break pull)
 };
 
 // Launchers (engine.cu).  `pass` is the global pass counter (its parity picks

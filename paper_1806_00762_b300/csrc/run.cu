@@ -701,6 +701,10 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             {
                 AlgoArgs ap = a;
                 ap.packed = chunks[win[0]].packed;  // windows hold one form (hybrid needs W = 1)
+                // every vertex with level <= k is final after k sweeps (strong prediction
+                // skips them), so an attempted vertex's level is at least k + 1; without
+                // prediction only the source has level 0
+                ap.bfs_lb = (pred_now && P->pvu == SERAPH_PVU_STRONG) ? (uint32_t)S.sweeps + 1u : 1u;
                 launch_relax(algo, P->kahan, ap, pass, (uint32_t)t, relax_grid, cs.s);
             }
             if (prof) SR_CUDA(cudaEventRecord(pr_e[(t % ring) * max_passes + j].e, cs.s));
