@@ -252,7 +252,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CHECK(slot_bytes >= 256, SERAPH_EBUDGET, "budget too small for the ring");
     // Pages [0, npk) stream packed, the rest plain (npk = 0 or P for one form).
     // Chunks are runs of consecutive pages of one form that fit a slot.
-    auto make_chunks = [&](uint32_t npk, std::vector<Chunk>& out) {
+    // Returns false (or throws SERAPH_EBUDGET when `strict`) if a page does not
+    // fit a slot in its form.
+    auto make_chunks = [&](uint32_t npk, std::vector<Chunk>& out, bool strict) {
         out.clear();
         Chunk cur{};
         bool open = false;
@@ -261,9 +263,12 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             const bool pk = p < npk;
             const uint64_t sb = pk ? pm.pk_bytes : pm.s_bytes;
             const uint64_t wb = use_w ? pm.w_bytes : 0;
-            SR_CHECK(align_up(sb, 256) + wb <= slot_bytes, SERAPH_EBUDGET,
-                     "page " + std::to_string(p) + " (" + std::to_string(sb + wb) +
-                         " B) does not fit a ring slot of " + std::to_string(slot_bytes) + " B");
+            if (align_up(sb, 256) + wb > slot_bytes) {
+                SR_CHECK(!strict, SERAPH_EBUDGET,
+                         "page " + std::to_string(p) + " (" + std::to_string(sb + wb) +
+                             " B) does not fit a ring slot of " + std::to_string(slot_bytes) + " B");
+                return false;
+            }
             if (open && cur.packed == pk && align_up(cur.s_bytes + sb, 256) + cur.w_bytes + wb <= slot_bytes) {
                 cur.end_page = p + 1;
                 cur.s_bytes += sb;
@@ -277,6 +282,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             open = true;
         }
         if (open) out.push_back(cur);
+        return true;
     };
     std::vector<Chunk> chunks;
     uint32_t npk = any_packed ? g->num_pages : 0;
@@ -286,14 +292,13 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         // are short) with which every chunk stays resident in the ring
         std::vector<Chunk> trial;
         uint32_t lo = 0, hi = g->num_pages;
-        while (lo < hi) {
+        while (lo < hi) {  // (a split whose plain pages do not fit a slot counts as too few)
             const uint32_t mid = (lo + hi) / 2;
-            make_chunks(mid, trial);
-            if (trial.size() <= R) hi = mid; else lo = mid + 1;
+            if (make_chunks(mid, trial, false) && trial.size() <= R) hi = mid; else lo = mid + 1;
         }
         npk = lo;
     }
-    make_chunks(npk, chunks);
+    make_chunks(npk, chunks, true);
     const bool packed = npk > 0;  // some pages stream packed
     for (auto& c : chunks) c.w_slot_off = align_up(c.s_bytes, 256);
     const uint32_t C = (uint32_t)chunks.size();

@@ -182,3 +182,18 @@ def test_hybrid_needs_window_one(r13p):
     with pytest.raises(SeraphError, match="EINVAL"):
         seraph.run(r13p["gr"], "bfs", columns="hybrid", window=2,
                    budget_bytes=packed_budget(r13p["gr"], 3, False))
+
+
+def test_hybrid_packs_pages_too_big_for_a_plain_slot(r13p):
+    """A slot smaller than the largest plain page but not the largest packed
+    one: the plain form is refused (SERAPH_EBUDGET), the hybrid form packs up to
+    and past every page that needs it and runs."""
+    g = r13p["gr"]
+    i = g.info()
+    assert i["max_page_packed_bytes"] < i["max_page_struct_bytes"]
+    slot = (i["max_page_packed_bytes"] + i["max_page_struct_bytes"]) // 2
+    kw = dict(source=5, window=1, slots=8, budget_bytes=8 * (slot // 256 * 256))
+    with pytest.raises(SeraphError, match="EBUDGET"):
+        seraph.run(g, "bfs", columns="plain", **kw)
+    got, _ = seraph.run(g, "bfs", columns="hybrid", **kw)
+    assert np.array_equal(got, r13p["bfs"])
