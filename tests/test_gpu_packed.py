@@ -184,16 +184,29 @@ def test_hybrid_needs_window_one(r13p):
                    budget_bytes=packed_budget(r13p["gr"], 3, False))
 
 
-def test_hybrid_packs_pages_too_big_for_a_plain_slot(r13p):
-    """A slot smaller than the largest plain page but not the largest packed
-    one: the plain form is refused (SERAPH_EBUDGET), the hybrid form packs up to
-    and past every page that needs it and runs."""
-    g = r13p["gr"]
+def test_hybrid_packs_pages_too_big_for_a_plain_slot():
+    """A hub page whose plain form exceeds a slot while its packed form fits
+    (its in-list is 1-byte gaps): the plain form is refused (SERAPH_EBUDGET),
+    the hybrid form packs the leading pages and runs.  (Pages of many small
+    in-lists can be larger packed than plain: the byte offsets cost 4 bytes
+    per vertex, which is why only leading pages are packed.)"""
+    n = 4096
+    rng = np.random.default_rng(2)
+    src = np.concatenate([np.arange(1, n), rng.integers(0, n, 3000)]).astype(np.uint32)
+    dst = np.concatenate([np.zeros(n - 1), rng.integers(1, n, 3000)]).astype(np.uint32)
+    w = synth.weights(src, dst)
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=6, compress=True)
+    og = oracle_graph(n, src, dst, w)
+    col_off, _, _ = oracle.csc(og)
     i = g.info()
-    assert i["max_page_packed_bytes"] < i["max_page_struct_bytes"]
-    slot = (i["max_page_packed_bytes"] + i["max_page_struct_bytes"]) // 2
-    kw = dict(source=5, window=1, slots=8, budget_bytes=8 * (slot // 256 * 256))
+    pages = g.page_bounds()
+    first_plain = 4 * (int(pages[1]) + 1) + 4 * int(col_off[pages[1]])
+    assert first_plain > 12000
+    kw = dict(source=1, window=1, slots=8, budget_bytes=8 * 12288)
     with pytest.raises(SeraphError, match="EBUDGET"):
         seraph.run(g, "bfs", columns="plain", **kw)
     got, _ = seraph.run(g, "bfs", columns="hybrid", **kw)
-    assert np.array_equal(got, r13p["bfs"])
+    assert np.array_equal(got, oracle.bfs(og, 1))
+    d, _ = seraph.run(g, "sssp", columns="hybrid", source=1, window=1, slots=8,
+                      budget_bytes=8 * (12288 + (i["max_page_weight_bytes"] + 255) // 256 * 256))
+    assert np.array_equal(d, oracle.sssp(og, 1))
