@@ -204,7 +204,19 @@ typedef struct seraph_params {
                                    use column 0 as their unconditional tick   */
     uint8_t  fsm_skip_mask;     /* bit s set: state s skips the update        */
     uint8_t  kahan;             /* PageRank: 1 = compensated FP32 sums        */
-    uint8_t  pad0[2];
+    uint8_t  pr_normalize;      /* PageRank (not in the paper): 1 = at every
+                                   sweep end whose total sum(x) is off 1 by
+                                   more than 2^-22, scale x (and x / outdeg)
+                                   by 1 / sum(x).  The fixpoint sums to 1
+                                   (summing its equation over all vertices
+                                   gives sum = (1-d) + d sum), so it never
+                                   moves; the scaling removes the error along
+                                   the fixpoint's own direction, which the
+                                   steps' in-place (Gauss-Seidel) updates with
+                                   a dangling mass one sweep old leave behind
+                                   and which otherwise decays only by about d
+                                   per sweep.  0 = off                        */
+    uint8_t  pad0;
     uint32_t max_sweeps;
     double   damping;           /* PageRank d                                 */
     double   tol;               /* PageRank stop: L1 change < tol             */

@@ -57,7 +57,7 @@ class GraphInfo(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("algo", i32), ("source", u32), ("budget_bytes", u64), ("window", u32),
                 ("passes", u32), ("pvu", i32), ("verify", u32), ("fsm_next", u8 * 12),
-                ("fsm_skip_mask", u8), ("kahan", u8), ("pad0", u8 * 2), ("max_sweeps", u32),
+                ("fsm_skip_mask", u8), ("kahan", u8), ("pr_normalize", u8), ("pad0", u8), ("max_sweeps", u32),
                 ("damping", dbl), ("tol", dbl), ("pr_fail_eps", dbl),
                 ("pr_pvu_off_below", dbl), ("thread_max_deg", u32), ("warp_max_deg", u32),
                 ("sched", i32), ("timeout_ms", u32), ("profile", u32), ("order", u32),

@@ -215,6 +215,7 @@ int seraph_params_default(seraph_params* p, int algo) {
         std::memcpy(p->fsm_next, fsm, 12);
         p->fsm_skip_mask = (1u << 2) | (1u << 3) | (1u << 4);
         p->kahan = 1;
+        p->pr_normalize = 1;
         p->max_sweeps = algo == SERAPH_PAGERANK ? 100 : 1000000;
         p->damping = 0.85;
         p->tol = 1e-7;

@@ -954,23 +954,109 @@ __global__ void close_min_kernel(RunState* rs, SweepReport* out) {
     rs->cur = SweepReport{};
 }
 
-// PageRank sweep close, one pass over the vertices: FP64 partial sums of the
-// dangling mass D = sum of x over out-degree-0 vertices and of the L1 change
-// |x - x_prev| against the last sweep end, then the snapshot x_prev = x.
-// |x - x_prev| in FP32 is exact whenever the two are within a factor of two
-// (Sterbenz), else correctly rounded; the sums are FP64.
-__global__ void __launch_bounds__(kNT) pr_close_partial_kernel(const float* x, float* x_prev,
-                                                               const float* inv_out, uint64_t n,
-                                                               double* part_r, double* part_d) {
+// Fixed-order FP64 reduction of `nparts` partials by one block.
+__device__ double reduce_partials(const double* partial, int nparts, double* ws) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += kNT) s += partial[i];
+    double tot;
+    block_excl_scan<kNT>(s, ws, &tot);
+    return tot;
+}
+
+// The sweep-close kernels stream whole vertex arrays: 16-byte vector accesses
+// when every array is 16-byte aligned (the tail, or everything otherwise, one
+// element at a time), all loads of an element before its stores.  The
+// element -> thread mapping depends only on n and the grid, so the partial
+// sums are deterministic.
+__device__ __forceinline__ bool aligned16(const void* a, const void* b = nullptr,
+                                          const void* c = nullptr, const void* d = nullptr) {
+    return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+             reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+}
+
+// Total PageRank mass sum(x): per-thread partials in compensated FP32, FP64
+// across threads and blocks in a fixed order.
+__global__ void __launch_bounds__(kNT) pr_mass_partial_kernel(const float* __restrict__ x,
+                                                              uint64_t n, double* part_s) {
     __shared__ double ws[kNT / 32 + 1];
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n4 = aligned16(x) ? n / 4 : 0;
+    SumAcc ss{0.f, 0.f};
+    for (uint64_t i = tid; i < n4; i += stride) {
+        const float4 v = reinterpret_cast<const float4*>(x)[i];
+        sum_add<true>(ss, v.x);
+        sum_add<true>(ss, v.y);
+        sum_add<true>(ss, v.z);
+        sum_add<true>(ss, v.w);
+    }
+    for (uint64_t v = 4 * n4 + tid; v < n; v += stride) sum_add<true>(ss, x[v]);
+    double tot;
+    block_excl_scan<kNT>((double)ss.s - (double)ss.c, ws, &tot);
+    if (threadIdx.x == 0) part_s[blockIdx.x] = tot;
+}
+
+// The fixpoint sums to 1, so a sweep end whose sum is further than 2^-22 from
+// it is scaled back onto the unit sum; closer than that (a few FP32 ulps of
+// 1) the values are left alone, so converged values can freeze.
+__global__ void __launch_bounds__(kNT) pr_mass_final_kernel(RunState* rs, const double* part_s,
+                                                            int nparts) {
+    __shared__ double ws[kNT / 32 + 1];
+    const double m = reduce_partials(part_s, nparts, ws);
+    if (threadIdx.x == 0)
+        rs->scale = (m > 0.0 && fabs(m - 1.0) > 0x1p-22) ? (float)(1.0 / m) : 1.0f;
+}
+
+// One vertex of the sweep close: scaled value (when sc != 1), its L1 change
+// against the last sweep end and, for a dangling vertex, its mass.
+__device__ __forceinline__ float close_vertex(float xv, float xp, float io, float sc, SumAcc& rr,
+                                              SumAcc& dd) {
+    if (sc != 1.0f) xv *= sc;
+    sum_add<true>(rr, fabsf(xv - xp));
+    if (io == 0.0f) sum_add<true>(dd, xv);
+    return xv;
+}
+
+// PageRank sweep close, one pass over the vertices: the optional mass
+// scaling (x and contrib = x / outdeg rewritten when rs->scale != 1), FP64
+// partial sums of the dangling mass D = sum of x over out-degree-0 vertices
+// and of the L1 change |x - x_prev| against the last sweep end, then the
+// snapshot x_prev = x.  |x - x_prev| in FP32 is exact whenever the two are
+// within a factor of two (Sterbenz), else correctly rounded; the sums are FP64.
+__global__ void __launch_bounds__(kNT) pr_close_partial_kernel(
+    float* __restrict__ x, float* __restrict__ contrib, float* __restrict__ x_prev,
+    const float* __restrict__ inv_out, uint64_t n, const RunState* rs, double* part_r,
+    double* part_d) {
+    __shared__ double ws[kNT / 32 + 1];
+    const float sc = rs ? rs->scale : 1.0f;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n4 = aligned16(x, contrib, x_prev, inv_out) ? n / 4 : 0;
     // per-thread partials (a few hundred terms) in compensated FP32 -- FP64
     // arithmetic is scarce on this GPU -- then FP64 across threads and blocks
     SumAcc rr{0.f, 0.f}, dd{0.f, 0.f};
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-         v += (uint64_t)gridDim.x * blockDim.x) {
-        const float xv = x[v];
-        sum_add<true>(rr, fabsf(xv - x_prev[v]));
-        if (inv_out[v] == 0.0f) sum_add<true>(dd, xv);
+    for (uint64_t i = tid; i < n4; i += stride) {
+        float4 xv = reinterpret_cast<const float4*>(x)[i];
+        const float4 xp = reinterpret_cast<const float4*>(x_prev)[i];
+        const float4 io = reinterpret_cast<const float4*>(inv_out)[i];
+        xv.x = close_vertex(xv.x, xp.x, io.x, sc, rr, dd);
+        xv.y = close_vertex(xv.y, xp.y, io.y, sc, rr, dd);
+        xv.z = close_vertex(xv.z, xp.z, io.z, sc, rr, dd);
+        xv.w = close_vertex(xv.w, xp.w, io.w, sc, rr, dd);
+        if (sc != 1.0f) {
+            reinterpret_cast<float4*>(x)[i] = xv;
+            reinterpret_cast<float4*>(contrib)[i] =
+                make_float4(xv.x * io.x, xv.y * io.y, xv.z * io.z, xv.w * io.w);
+        }
+        reinterpret_cast<float4*>(x_prev)[i] = xv;
+    }
+    for (uint64_t v = 4 * n4 + tid; v < n; v += stride) {
+        const float io = inv_out[v];
+        const float xv = close_vertex(x[v], x_prev[v], io, sc, rr, dd);
+        if (sc != 1.0f) {
+            x[v] = xv;
+            contrib[v] = xv * io;
+        }
         x_prev[v] = xv;
     }
     const double r = (double)rr.s - (double)rr.c, d = (double)dd.s - (double)dd.c;
@@ -979,15 +1065,6 @@ __global__ void __launch_bounds__(kNT) pr_close_partial_kernel(const float* x, f
     if (threadIdx.x == 0) part_r[blockIdx.x] = tot;
     block_excl_scan<kNT>(d, ws, &tot);
     if (threadIdx.x == 0) part_d[blockIdx.x] = tot;
-}
-
-// Fixed-order FP64 reduction of `nparts` partials by one block.
-__device__ double reduce_partials(const double* partial, int nparts, double* ws) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += kNT) s += partial[i];
-    double tot;
-    block_excl_scan<kNT>(s, ws, &tot);
-    return tot;
 }
 
 // Residual and dangling mass of the sweep; base term (1-d)/n + d D/n for the
@@ -1121,8 +1198,14 @@ void launch_close_min(RunState* rs, SweepReport* out, cudaStream_t s) {
 }
 
 void launch_close_pr(const AlgoArgs& a, uint64_t n, float* x_prev, double damping,
-                     double* partial, int nparts, SweepReport* out, cudaStream_t s) {
-    pr_close_partial_kernel<<<nparts, kNT, 0, s>>>(a.x, x_prev, a.inv_out, n, partial,
+                     double* partial, int nparts, SweepReport* out, bool normalize,
+                     cudaStream_t s) {
+    if (normalize) {
+        pr_mass_partial_kernel<<<nparts, kNT, 0, s>>>(a.x, n, partial + 2 * nparts);
+        pr_mass_final_kernel<<<1, kNT, 0, s>>>(a.rs, partial + 2 * nparts, nparts);
+    }
+    pr_close_partial_kernel<<<nparts, kNT, 0, s>>>(a.x, a.contrib, x_prev, a.inv_out, n,
+                                                    normalize ? a.rs : nullptr, partial,
                                                     partial + nparts);
     pr_close_final_kernel<<<1, kNT, 0, s>>>(a.rs, partial, partial + nparts, nparts, n, damping,
                                              out);

@@ -55,7 +55,8 @@ struct RunState {
     unsigned int list_cnt[2][8];
     unsigned int work[2][8];
     unsigned int thr_cur, thr_prev, sweeps_done, err;
-    float base, pad;
+    float base;
+    float scale;              // PageRank: 1 / sum(x) applied at the sweep close (1 = none)
     double dsum, rsum;
 };
 
@@ -126,6 +127,7 @@ void launch_init_pr(const uint32_t* outdeg, const AlgoArgs& a, float* x_prev, ui
                     cudaStream_t s);
 void launch_close_min(RunState* rs, SweepReport* out, cudaStream_t s);
 void launch_close_pr(const AlgoArgs& a, uint64_t n, float* x_prev, double damping,
-                     double* partial, int nparts, SweepReport* out, cudaStream_t s);
+                     double* partial, int nparts, SweepReport* out, bool normalize,
+                     cudaStream_t s);
 
 }  // namespace seraph

@@ -376,7 +376,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     DevBuf<double> partial;
     if (is_pr) {
         ensure(x, n); ensure(contrib, n); ensure(x_next, n); ensure(x_prev, n); ensure(inv_out, n);
-        partial.alloc(2 * nparts);
+        partial.alloc(3 * nparts);
     } else {
         ensure(val, n);
     }
@@ -430,7 +430,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         SR_CUDA(cudaMemcpyAsync(rs.p, &init, sizeof(init), cudaMemcpyHostToDevice, cs.s));
         if (is_pr) {
             launch_init_pr(g->d_outdeg.p, a, x_prev.p, n, cs.s);
-            launch_close_pr(a, n, x_prev.p, P->damping, partial.p, nparts, nullptr, cs.s);
+            launch_close_pr(a, n, x_prev.p, P->damping, partial.p, nparts, nullptr, false, cs.s);
             launches += 3;
         } else {
             uint32_t source = P->source;
@@ -736,10 +736,11 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
 
         // ---------------------------------------------------- sweep close
         if (is_pr)
-            launch_close_pr(a, n, x_prev.p, P->damping, partial.p, nparts, d_rep.p, cs.s);
+            launch_close_pr(a, n, x_prev.p, P->damping, partial.p, nparts, d_rep.p,
+                            P->pr_normalize != 0, cs.s);
         else
             launch_close_min(rs.p, d_rep.p, cs.s);
-        launches += is_pr ? 2 : 1;
+        launches += is_pr ? (P->pr_normalize ? 4 : 2) : 1;
         SR_CUDA(cudaMemcpyAsync(h_rep.p, d_rep.p, sizeof(SweepReport), cudaMemcpyDeviceToHost, cs.s));
         SR_CUDA(cudaMemcpyAsync(h_steps.p, d_steps.p, ring * sizeof(unsigned), cudaMemcpyDeviceToHost, cs.s));
         const uint64_t rows_now = std::min<uint64_t>(t + 1 - sweep_first_step, rec_rows);
