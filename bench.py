@@ -4,7 +4,8 @@ path on R-MAT-28 (2^28 vertices, edge factor 16, a,b,c,d = .57,.19,.19,.05),
 budget, vertex arrays resident in HBM, SSSP (weights in [1,255], from vertex
 0) and PageRank (FP32 Kahan sums, FP64 residual, L1 < 1e-7 or 100 sweeps),
 predictive vertex updating on (strong conditions for SSSP, the weak state
-machine for PageRank), fixed (non-learned) schedules per algorithm.
+machine for PageRank; PageRank's values rescaled to unit sum at sweep ends),
+fixed (non-learned) schedules per algorithm.
 
 Besides the timed steps, one run of each algorithm with the paper's plain
 schedule -- a sliding window of k = 4 chunks over a ring of 5 slots, cyclic
@@ -40,7 +41,7 @@ METRIC = "time-to-fixpoint and effective GTEPS, RMAT-28 streamed; learned vs fix
 
 
 DEFAULT_SSSP = "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid"
-DEFAULT_PAGERANK = "order=zigzag,window=1,slots=12,pvu=weak,columns=hybrid"
+DEFAULT_PAGERANK = "order=zigzag,window=1,slots=12,pvu=weak,columns=hybrid,pr_normalize=1"
 
 
 def parse():
@@ -508,11 +509,12 @@ def main():
     }
     if not args.no_paper_schedule:
         plain = dict(order="cyclic", window=4, slots=5, pvu="weak", columns="plain")
-        p1, p2 = step(plain, plain)
+        p1, p2 = step(plain, dict(plain, pr_normalize=0))
         p_bytes = (algo_bytes("sssp", p1, ww, True) + algo_bytes("pagerank", p2, ww, True))
         p_time = (p1["time_ms"] + p2["time_ms"]) / 1e3
         line["paper_schedule"] = {
-            "schedule": plain, "time_to_fixpoint_s": {"sssp": p1["time_ms"] / 1e3,
+            "schedule": {"sssp": plain, "pagerank": dict(plain, pr_normalize=0)},
+            "time_to_fixpoint_s": {"sssp": p1["time_ms"] / 1e3,
                                                        "pagerank": p2["time_ms"] / 1e3},
             "sweeps": {"sssp": p1["sweeps"], "pagerank": p2["sweeps"]},
             "gteps": 2 * E / p_time / 1e9,
@@ -522,7 +524,8 @@ def main():
         # baseline: one pass per streamed page pair (double buffer, no reuse), no prediction;
         # psi: k = 4 local passes over a window of 4 chunks while the next streams (Fig. 4);
         # psi+pvu: with the predictive vertex update (strong for SSSP, weak for PageRank);
-        # then this build's schedule without and with packed SSSP pages.
+        # then this build's schedule without and with packed SSSP pages, hybrid pages, and
+        # PageRank's unit-sum scaling at sweep ends (off in every row before the last).
         ladder = [
             ("baseline", dict(order="cyclic", window=1, slots=2, pvu="off", columns="plain"),
              dict(order="cyclic", window=1, slots=2, pvu="off", columns="plain")),
@@ -536,6 +539,9 @@ def main():
              dict(sched["pagerank"], slots=32, columns="plain")),
             ("resident+pvu+hybrid", sched["sssp"], sched["pagerank"]),
         ]
+        ladder = [(nm, ks, dict(kp, pr_normalize=0)) for nm, ks, kp in ladder]
+        ladder.append(("resident+pvu+hybrid+pr_unit_sum", sched["sssp"],
+                       dict(sched["pagerank"], pr_normalize=1)))
         line["ablation"] = {}
         for name, ks, kp in ladder:
             a1, a2 = step(ks, kp)
