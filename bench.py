@@ -166,7 +166,7 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True)
 # DRAM traffic of the relax kernels per launch on this workload, from one ncu
 # capture of the default step (profiles/launches_rmat28_sssp_pagerank.md);
 # valid only for the kernel source it was taken on.
-RELAX_TRAFFIC = {"engine_sha256": "cae364623736d829", "bytes_per_launch": 6.816621504e9,
+RELAX_TRAFFIC = {"engine_sha256": "1bdb20f0db393ced", "bytes_per_launch": 6.183436262e9,
                  "workload": "rmat28 default step"}
 
 
@@ -181,6 +181,14 @@ def relax_traffic(args) -> float | None:
     if sha != RELAX_TRAFFIC["engine_sha256"] or not default:
         return None
     return RELAX_TRAFFIC["bytes_per_launch"]
+
+
+def gather_ceiling(seraph) -> float:
+    """Random 4-byte gathers per second when every gather hits L2: 2^29 reads
+    of 2^28 values, all inside an 8 MB evict-last range (seraph_gather_probe,
+    best of 5 launches).  It bounds a pull pass whose gathers all hit L2."""
+    n_gathers = 1 << 29
+    return n_gathers / seraph.gather_probe(1 << 28, n_gathers, (8 << 20) // 4, 1.0, reps=5)
 
 
 def pipeline_roofline(hbm_bytes: float, link_bytes: float, seconds: float, hbm_gbs: float,
@@ -479,6 +487,9 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     achieved = relax_bytes / (relax_ms / 1e3) / 1e9 if relax_ms else 0.0
+    gathers = sum(s1["edges_relaxed"] + s2["edges_relaxed"] for s1, s2 in stats)
+    gather_rate = gathers / (relax_ms / 1e3) / 1e9 if relax_ms else 0.0
+    gather_peak = gather_ceiling(seraph) / 1e9
     s1, s2 = stats[-1]
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
@@ -497,6 +508,12 @@ def main():
                      "traffic": relax_traffic(args),
                      "algorithmic_bytes_per_launch": relax_bytes / relax_launches if relax_launches else 0,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "gather_roofline": {"bound": "l2_gather_rate", "kernel": "relax_kernel",
+                            "achieved": gather_rate, "peak": gather_peak, "unit": "Ggathers/s",
+                            "frac": gather_rate / gather_peak if gather_peak else 0.0,
+                            "peak_source": "seraph_gather_probe: 2^29 random 4-byte gathers "
+                                           "of 2^28 values, all in an 8 MB evict-last range "
+                                           "(every gather an L2 hit), best of 5, this process"},
         "link_roofline": {"bound": "link", "achieved": streamed / (dev_s * 1e9) if dev_s else 0,
                           "peak": link, "unit": "GB/s",
                           "frac": (streamed / (link * 1e9)) / dev_s if dev_s else 0,

@@ -342,6 +342,31 @@ int seraph_pull_fixpoint_noalloc(int algo, uint64_t n, const uint64_t* col_off,
                                  uint32_t* values, uint32_t* passes_out, void* stream);
 
 /*
+ * Random-gather probe (not in the paper; a measurement aid).
+ *
+ * Times the relax kernels' inner operation in isolation: n_gathers 4-byte
+ * reads of a device array of n_values values, at indexes that stream in
+ * order (16-byte loads, L2 evict-first) and are drawn by a counter-based hash
+ * uniformly from [0, hot_values) with probability hot_frac, else from
+ * [hot_values, n_values).  Reads of the hot range carry L2 evict-last hints
+ * under a persisting-L2 set-aside of 4 * hot_values bytes (the context's
+ * previous limit comes back on return), as in seraph_run.  One warm-up
+ * launch, then `reps` timed launches (CUDA events on `stream`, NULL = the
+ * default stream); *best_seconds (host) receives the fastest.  With every
+ * index in a range far smaller than L2 it measures the rate of random gathers
+ * that hit L2 -- the ceiling of a pull pass whose gathers all hit -- and with
+ * cold indexes the cost of DRAM misses.
+ *
+ * Allocates 4 * n_values + 4.5 * n_gathers bytes of device memory for the
+ * call.  Errors: SERAPH_EINVAL (n_values 0 or >= 2^32, n_gathers not a
+ * positive multiple of 8, hot_values > n_values, hot_frac outside [0, 1],
+ * reps 0, best_seconds NULL -- all checked before any device call),
+ * SERAPH_ENOMEM, SERAPH_ECUDA.
+ */
+int seraph_gather_probe(uint64_t n_values, uint64_t n_gathers, uint64_t hot_values,
+                        double hot_frac, uint32_t reps, void* stream, double* best_seconds);
+
+/*
  * Learned scheduler (not in the paper; its closest counterpart is the
  * fine-grained idle-slot scheduling of Sec. 3.2).  A 16 -> 64 -> 64 -> 17 MLP
  * with GELU, BF16 weights and FP32 accumulation (FP32 master weights, Adam),

@@ -282,6 +282,18 @@ def run(graph: Graph, algo, out=None, stream=None, **kw):
     return out, st.as_dict()
 
 
+def gather_probe(n_values, n_gathers, hot_values, hot_frac=1.0, reps=5, stream=None) -> float:
+    """Fastest of `reps` timed launches (seconds) of the random-gather probe:
+    n_gathers 4-byte reads of n_values device values, a fraction hot_frac of
+    them uniform over the first hot_values (L2 evict-last), the rest uniform
+    over the others (seraph_gather_probe in include/seraph.h)."""
+    sec = ctypes.c_double(0.0)
+    C.check(C.lib().seraph_gather_probe(int(n_values), int(n_gathers), int(hot_values),
+                                        float(hot_frac), int(reps), _stream_ptr(stream),
+                                        ctypes.byref(sec)))
+    return sec.value
+
+
 class BGraph:
     """Device-resident out-edge CSR for batched queries."""
 

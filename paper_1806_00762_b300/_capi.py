@@ -122,6 +122,8 @@ PROTOTYPES = {
                                   ctypes.POINTER(Stats)]),
     "seraph_pull_fixpoint_noalloc": (ctypes.c_int, [ctypes.c_int, u64, vp, vp, vp, u32, vp, vp,
                                                     vp]),
+    "seraph_gather_probe": (ctypes.c_int, [u64, u64, u64, dbl, u32, vp,
+                                           ctypes.POINTER(dbl)]),
     "seraph_sched_create": (ctypes.c_int, [u64, ctypes.c_int, ctypes.POINTER(vp)]),
     "seraph_sched_get_params": (ctypes.c_int, [vp, vp]),
     "seraph_sched_set_params": (ctypes.c_int, [vp, vp]),

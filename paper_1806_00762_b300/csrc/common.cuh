@@ -37,6 +37,36 @@ struct Error : std::runtime_error {
 
 int device_sms();
 
+// Evict-last lines live in the L2 set-aside for persisting accesses, which is
+// empty unless the context limit is raised.  Held for one run, then the
+// persisting lines are reset to normal and the previous limit comes back (a
+// context limit: nothing outlasts the process).
+struct PersistingL2 {
+    bool set = false;
+    size_t prev = 0;
+    void reserve(int device, uint64_t bytes) {
+        int maxp = 0;
+        if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, device) != cudaSuccess ||
+            maxp <= 0) {
+            (void)cudaGetLastError();
+            return;
+        }
+        if (cudaDeviceGetLimit(&prev, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
+        const size_t want = bytes < (uint64_t)maxp ? (size_t)bytes : (size_t)maxp;
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) set = true;
+        else (void)cudaGetLastError();
+    }
+    ~PersistingL2() {
+        if (!set) return;
+        (void)cudaCtxResetPersistingL2Cache();
+        (void)cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, prev);
+        (void)cudaGetLastError();
+    }
+};
+
 // Device allocation owned by the library.
 template <class T>
 struct DevBuf {

@@ -45,36 +45,6 @@ struct Chunk {
     bool packed;                // pages in the packed form (else plain)
 };
 
-// Evict-last lines live in the L2 set-aside for persisting accesses, which is
-// empty unless the context limit is raised.  Held for one run, then the
-// persisting lines are reset to normal and the previous limit comes back (a
-// context limit: nothing outlasts the process).
-struct PersistingL2 {
-    bool set = false;
-    size_t prev = 0;
-    void reserve(int device, uint64_t bytes) {
-        int maxp = 0;
-        if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, device) != cudaSuccess ||
-            maxp <= 0) {
-            (void)cudaGetLastError();
-            return;
-        }
-        if (cudaDeviceGetLimit(&prev, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return;
-        }
-        const size_t want = std::min<uint64_t>(bytes, (uint64_t)maxp);
-        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) set = true;
-        else (void)cudaGetLastError();
-    }
-    ~PersistingL2() {
-        if (!set) return;
-        (void)cudaCtxResetPersistingL2Cache();
-        (void)cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, prev);
-        (void)cudaGetLastError();
-    }
-};
-
 struct Event {
     cudaEvent_t e = nullptr;
     void create(bool timing) {

@@ -102,3 +102,26 @@ def test_sched_targets_on_a_handmade_trace():
     k, prio = tr.targets(0.95)
     assert list(k) == [2, 1, 16]
     assert abs(prio[0] - np.log2(101) / 24) < 1e-6 and prio[1] == 0.0
+
+
+def test_gather_probe_rejects_bad_arguments_before_any_device_call():
+    """Every argument check of seraph_gather_probe runs on the host first, so
+    it answers SERAPH_EINVAL without a GPU."""
+    import ctypes
+    lib = C.lib()
+    sec = ctypes.c_double(0.0)
+    bad = [
+        (0, 8, 0, 1.0, 1),            # no values
+        (1 << 32, 8, 0, 1.0, 1),      # 2^32 values
+        (16, 0, 0, 1.0, 1),           # no gathers
+        (16, 12, 0, 1.0, 1),          # not a multiple of 8
+        (16, 8, 17, 1.0, 1),          # hot range beyond the values
+        (16, 8, 4, 1.5, 1),           # fraction above 1
+        (16, 8, 4, -0.1, 1),          # fraction below 0
+        (16, 8, 4, 0.5, 0),           # no timed launch
+    ]
+    for nv, ng, hot, frac, reps in bad:
+        rc = lib.seraph_gather_probe(nv, ng, hot, frac, reps, None, ctypes.byref(sec))
+        assert rc == C.SERAPH_EINVAL, (nv, ng, hot, frac, reps)
+        assert lib.seraph_last_error()
+    assert lib.seraph_gather_probe(16, 8, 4, 0.5, 1, None, None) == C.SERAPH_EINVAL
