@@ -657,7 +657,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             wd.nblocks = blocks;
         }
         const bool pred_now = is_pr ? (predict && !pr_predict_off) : predict;
-        npass = max_passes > P->passes && (prefetch || resident || learned) ? max_passes : P->passes;
+        npass = max_passes > P->passes && (prefetch || learned) ? max_passes : P->passes;
         const uint64_t row = t - sweep_first_step;
         unsigned* rec_row = track && row < rec_rows ? rec_gain.p + row * 16 : nullptr;
         if (track) {
