@@ -41,7 +41,7 @@ METRIC = "time-to-fixpoint and effective GTEPS, RMAT-28 streamed; learned vs fix
 
 
 DEFAULT_SSSP = "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid"
-DEFAULT_PAGERANK = "order=zigzag,window=1,slots=12,pvu=weak,columns=hybrid,pr_normalize=1,max_passes=2"
+DEFAULT_PAGERANK = "order=zigzag,window=1,slots=12,pvu=weak,columns=hybrid,pr_normalize=1"
 
 
 def parse():
