@@ -263,6 +263,14 @@ typedef struct seraph_params {
                                    and restores it on return.  0 = no hints;
                                    the default SERAPH_L2_HOT_AUTO = 3/8 of
                                    the device's L2.  Never changes a result. */
+    double   pr_omega;          /* PageRank over-relaxation (not in the paper):
+                                   a pass publishes x + omega (x_new - x),
+                                   clamped at 0, instead of x_new (successive
+                                   over-relaxation of the in-place steps; the
+                                   fixpoint is the same) until a sweep
+                                   changes x by less than pr_pvu_off_below
+                                   (L1); later sweeps publish x_new.  0 or 1
+                                   = plain updates; must lie in [0, 2)     */
 } seraph_params;
 
 #define SERAPH_L2_HOT_AUTO UINT64_MAX

@@ -64,7 +64,7 @@ class Params(ctypes.Structure):
                 ("max_passes", u32), ("slots", u32), ("group4_max_deg", u32),
                 ("group8_max_deg", u32),
                 ("sched_model", vp), ("stream", vp), ("trace", vp), ("columns", u32),
-                ("pad1", u32), ("l2_hot_bytes", u64)]
+                ("pad1", u32), ("l2_hot_bytes", u64), ("pr_omega", dbl)]
 
 
 class Stats(ctypes.Structure):

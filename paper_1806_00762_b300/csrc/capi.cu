@@ -228,6 +228,7 @@ int seraph_params_default(seraph_params* p, int algo) {
         p->sched = SERAPH_SCHED_FIXED;
         p->timeout_ms = 600000;
         p->l2_hot_bytes = SERAPH_L2_HOT_AUTO;
+        p->pr_omega = 1.0;
         return SERAPH_OK;
     });
 }

@@ -865,6 +865,8 @@ __global__ void __launch_bounds__(kNT, PK ? 4 : (ALGO == ALG_SSSP ? 5 : 6))
     flush_locals(a, par, step, L);
 }
 
+// Publishes a pass's new PageRank values (Jacobi within the pass): x and
+// contrib = x / outdeg of every attempted vertex, optionally over-relaxed.
 __global__ void __launch_bounds__(kNT) pr_apply_kernel(AlgoArgs a, uint32_t pass) {
     const int par = pass & 1;
     RunState* rs = a.rs;
@@ -874,7 +876,11 @@ __global__ void __launch_bounds__(kNT) pr_apply_kernel(AlgoArgs a, uint32_t pass
         const unsigned nk = rs->list_cnt[par][k];
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nk; i += stride) {
             const uint32_t v = (uint32_t)a.list[k][i];
-            const float xn = a.x_next[v];
+            float xn = a.x_next[v];
+            if (a.omega != 1.0f) {  // over-relaxed: x + omega (x_next - x), kept >= 0
+                const float xo = a.x[v];
+                xn = fmaxf(fmaf(a.omega, xn - xo, xo), 0.0f);
+            }
             a.x[v] = xn;
             a.contrib[v] = xn * a.inv_out[v];
         }

@@ -95,6 +95,7 @@ struct AlgoArgs {
     uint32_t n;               // vertices
     uint32_t bfs_lb;          // BFS: no attempted vertex can reach a level below this, so a
                               // lane that finds it stops scanning (early-break pull)
+    float omega;              // PageRank over-relaxation factor of the apply step (1 = plain)
 };
 
 // Launchers (engine.cu).  `pass` is the global pass counter (its parity picks

@@ -186,6 +186,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
              "weak prediction needs the verification sweep");
     SR_CHECK(out_mem == SERAPH_MEM_HOST || out_mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad out_mem");
     SR_CHECK(P->max_sweeps >= 1, SERAPH_EINVAL, "max_sweeps must be >= 1");
+    SR_CHECK(P->pr_omega >= 0.0 && P->pr_omega < 2.0, SERAPH_EINVAL, "pr_omega must be in [0, 2)");
     for (int i = 0; i < 12; ++i)
         SR_CHECK(P->fsm_next[i] < 6, SERAPH_EINVAL, "fsm_next entries must be < 6");
     SR_CHECK(P->thread_max_deg <= P->group4_max_deg && P->group4_max_deg <= P->group8_max_deg &&
@@ -371,6 +372,11 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     a.cls_max[3] = P->warp_max_deg;
     a.damping = (float)P->damping;
     a.fail_eps = (float)P->pr_fail_eps;
+    // over-relaxation runs while the last sweep changed the values by at least
+    // pr_pvu_off_below (L1); the sweeps after that publish plain updates, so
+    // no vertex keeps an overshoot from its last over-relaxed update
+    const float omega0 = (P->pr_omega == 0.0 || P->pr_omega == 1.0) ? 1.0f : (float)P->pr_omega;
+    a.omega = omega0;
     a.fsm_bits = 0;
     for (int i = 0; i < 12; ++i) a.fsm_bits |= (uint64_t)P->fsm_next[i] << (3 * i);
     a.skip_mask = P->fsm_skip_mask;
@@ -781,6 +787,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             S.residual = rep.resid;
             if (!pred_now && rep.resid < P->tol) { S.converged = 1; stop = true; }
             else if (pred_now && rep.resid < std::max(P->pr_pvu_off_below, P->tol)) pr_predict_off = true;
+            if (rep.resid < P->pr_pvu_off_below) a.omega = 1.0f;
             if (!stop && S.sweeps >= P->max_sweeps) stop = true;
         } else {
             bool all_after = true;

@@ -180,6 +180,25 @@ def test_rmat16_pagerank_mass_scaling(r16, pr_normalize):
         assert st["sweeps"] * 3 <= st0["sweeps"] * 2, (st["sweeps"], st0["sweeps"])
 
 
+@pytest.mark.parametrize("omega", [1.15, 1.3])
+def test_rmat16_pagerank_over_relaxed(r16, omega):
+    """Over-relaxed steps (x + omega (x_new - x) while the sweep change is above
+    pr_pvu_off_below, plain updates after) reach the same fixpoint."""
+    x, st = seraph.run(r16["g"], "pagerank", pr_omega=omega, **cfg1(r16["g"], False))
+    l1, rel = pr_errors(x, r16["pr"])
+    assert l1 <= PR_L1 and rel <= PR_REL, (l1, rel, st)
+    assert st["converged"] == 1 and st["residual"] < 1e-7
+    if omega == 1.15:
+        _, st1 = seraph.run(r16["g"], "pagerank", **cfg1(r16["g"], False))
+        assert st["sweeps"] <= st1["sweeps"], (st["sweeps"], st1["sweeps"])
+
+
+def test_pagerank_over_relaxation_out_of_range_is_rejected(r16):
+    for omega in (2.0, -0.5):
+        with pytest.raises(SeraphError, match="EINVAL"):
+            seraph.run(r16["g"], "pagerank", pr_omega=omega, **cfg1(r16["g"], False))
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 1027, 4099])
 def test_pagerank_ragged_vertex_counts(n):
     """Vertex counts that are not a multiple of four take the close kernels'
