@@ -167,7 +167,7 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True)
 # DRAM traffic of the relax kernels per launch on this workload, from one ncu
 # capture of the default step (profiles/launches_rmat28_sssp_pagerank.md);
 # valid only for the kernel source it was taken on.
-RELAX_TRAFFIC = {"engine_sha256": "1bdb20f0db393ced", "bytes_per_launch": 6.183436262e9,
+RELAX_TRAFFIC = {"engine_sha256": "12bf6fac3d30c341", "bytes_per_launch": 5.798483204e9,
                  "workload": "rmat28 default step"}
 
 
