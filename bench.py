@@ -167,9 +167,9 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True)
 # DRAM traffic of the relax kernels per launch on this workload, from one ncu
 # capture of the default step (profiles/launches_rmat28_sssp_pagerank.md);
 # valid only for the kernel source and the two schedules it was taken on.
-RELAX_TRAFFIC = {"engine_sha256": "12bf6fac3d30c341", "bytes_per_launch": 5.798483204e9,
+RELAX_TRAFFIC = {"engine_sha256": "12bf6fac3d30c341", "bytes_per_launch": 5.220801756e9,
                  "sssp": "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid",
-                 "pagerank": "order=zigzag,window=1,slots=12,pvu=weak,columns=hybrid,"
+                 "pagerank": "order=zigzag,window=1,slots=14,pvu=weak,columns=hybrid,"
                              "pr_normalize=1,pr_omega=1.15",
                  "workload": "rmat28 default step"}
 
