@@ -70,6 +70,8 @@ def _L():
     lib.oracle_bfs.argtypes = [c_u64, _u64p, _u32p, c_u32, _u32p]
     lib.oracle_cc.restype = None
     lib.oracle_cc.argtypes = [c_u64, _u64p, _u32p, _u32p]
+    lib.oracle_cc_edges.restype = None
+    lib.oracle_cc_edges.argtypes = [c_u64, c_u64, _u32p, _u32p, _u32p]
     lib.oracle_pagerank.restype = c_int
     lib.oracle_pagerank.argtypes = [c_u64, _u64p, _u32p, c_dbl, c_dbl, c_int, _f64p,
                                     ctypes.POINTER(c_dbl)]
@@ -240,6 +242,15 @@ def bfs(g: CSR, source: int) -> np.ndarray:
 def cc(g: CSR) -> np.ndarray:
     label = np.empty(g.n, dtype=np.uint32)
     _L().oracle_cc(g.n, g.row_off, g.col, label)
+    return label
+
+
+def cc_edges(n: int, src, dst) -> np.ndarray:
+    """Weakly connected components (min-id labels) straight from a raw edge
+    list: the union-find of ``cc`` without the CSR build (large graphs)."""
+    src, dst = _u32(src), _u32(dst)
+    label = np.empty(n, dtype=np.uint32)
+    _L().oracle_cc_edges(n, src.shape[0], src, dst, label)
     return label
 
 

@@ -210,6 +210,23 @@ void oracle_cc(uint64_t n, const uint64_t* row_off, const uint32_t* col, uint32_
     for (uint64_t v = 0; v < n; ++v) label[v] = uf_find(parent, (uint32_t)v);
 }
 
+/* The same union-find over a raw edge list: every (src[i], dst[i]) joins its
+ * two endpoints, whatever its direction, self-loops and duplicates included
+ * (they join nothing new).  Weakly connected components with min-id labels,
+ * without building a CSR first. */
+void oracle_cc_edges(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                     uint32_t* label)
+{
+    uint32_t* parent = label;
+    for (uint64_t v = 0; v < n; ++v) parent[v] = (uint32_t)v;
+    for (uint64_t i = 0; i < m; ++i) {
+        uint32_t a = uf_find(parent, src[i]), b = uf_find(parent, dst[i]);
+        if (a == b) continue;
+        if (a < b) parent[b] = a; else parent[a] = b;
+    }
+    for (uint64_t v = 0; v < n; ++v) label[v] = uf_find(parent, (uint32_t)v);
+}
+
 /* ------------------------------------------------------------- PageRank */
 
 typedef struct {

@@ -57,6 +57,8 @@ int  oracle_sssp(uint64_t n, const uint64_t* row_off, const uint32_t* col, const
 void oracle_bfs(uint64_t n, const uint64_t* row_off, const uint32_t* col, uint32_t source,
                 uint32_t* level);
 void oracle_cc(uint64_t n, const uint64_t* row_off, const uint32_t* col, uint32_t* label);
+void oracle_cc_edges(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                     uint32_t* label);
 
 /* FP64 PageRank.  Runs until the L1 change of one iteration is < tol or
  * maxit iterations; x receives the result.  Returns iterations run; *resid

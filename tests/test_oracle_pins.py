@@ -282,17 +282,18 @@ def test_cc_vs_reachability(seed):
     n = int(rng.integers(1, 65))
     src, dst, _ = graphs.random_graph(n, int(rng.integers(0, n + 1)), seed=seed)
     g = oracle.build_csr(n, src, dst)
-    lab = oracle.cc(g)
     R = np.eye(n, dtype=bool)
     for u, v in zip(src, dst):
         R[u, v] = R[v, u] = True
     for _ in range(max(1, int(np.ceil(np.log2(max(n, 2)))) + 1)):  # transitive closure
         R = (R.astype(np.int64) @ R.astype(np.int64)) > 0
-    for v in range(n):
-        comp = np.nonzero(R[v])[0]
-        assert lab[v] == comp.min()                         # label = min id
-        assert np.all(lab[comp] == lab[v])                  # equal iff connected
-        assert np.all(lab[np.nonzero(~R[v])[0]] != lab[v])
+    # the CSR form and the raw-edge form (self-loops and duplicates as drawn)
+    for lab in (oracle.cc(g), oracle.cc_edges(n, src, dst)):
+        for v in range(n):
+            comp = np.nonzero(R[v])[0]
+            assert lab[v] == comp.min()                         # label = min id
+            assert np.all(lab[comp] == lab[v])                  # equal iff connected
+            assert np.all(lab[np.nonzero(~R[v])[0]] != lab[v])
 
 
 def test_cc_vs_scipy_rmat():
@@ -308,6 +309,7 @@ def test_cc_vs_scipy_rmat():
     mins = np.full(k, g.n)
     np.minimum.at(mins, sc, np.arange(g.n))
     assert np.array_equal(lab, mins[sc].astype(np.uint32))
+    assert np.array_equal(oracle.cc_edges(g.n, src, dst), lab)  # raw edges, one direction each
 
 
 # -------------------------------------------------------------- PageRank
