@@ -1,9 +1,10 @@
 """Train the learned scheduler on traces of the fixed pipeline.
 
 Traces come from SSSP, BFS and PageRank runs on seeded R-MAT graphs built as
-the benchmark builds them (out-degree order, hybrid pages), at scale
-24 with small ring slots and at scale 28 with the benchmark's ring, each step
-running up to 16 local passes so that the gain of every extra pass is seen.
+the benchmark builds them (out-degree order, hybrid pages; PageRank with the
+unit-sum scaling and over-relaxed steps), at scale 24 with small ring slots
+and at scale 28 with the benchmark's rings, each step running up to 16 local
+passes so that the gain of every extra pass is seen.
 Targets (seraph_sched_targets): k = fewest passes holding 95 % of a step's
 changes, priority = log2(1 + first-pass changes) / 24.  Training uses the
 library's own forward/backward/Adam kernels.  The FP32 master weights are
@@ -40,16 +41,17 @@ def _graph(seraph, synth, torch, scale, pages):
     return g
 
 
-def collect(seraph, torch, g, budget, slots, runs):
+def collect(seraph, torch, g, budget, runs):
+    """runs: (algorithm, source, ring slots, extra seraph_params overrides)."""
     xs, ks, ps = [], [], []
     n = g.info()["n"]
-    for algo, source in runs:
+    for algo, source, slots, extra in runs:
         tr = seraph.TraceBuffer(500_000)
         out = torch.empty(n, dtype=torch.float32 if algo == "pagerank" else torch.int32,
                           device="cuda")
         # the benchmark's page form: hybrid (leading pages packed, the rest plain)
         seraph.run(g, algo, out=out, source=source, window=1, slots=slots, passes=16, trace=tr,
-                   budget_bytes=budget, columns="hybrid")
+                   budget_bytes=budget, columns="hybrid", **extra)
         f, _, _ = tr.rows()
         k, p = tr.targets(0.95)
         xs.append(f.copy())
@@ -79,14 +81,18 @@ def main():
     t0 = time.time()
     xs, ks, ps = [], [], []
     for scale in (int(s) for s in args.scales.split(",")):
+        # PageRank as the benchmark runs it: unit-sum scaling (the library's
+        # default) and steps over-relaxed by 1.15
+        pr = {"pr_omega": 1.15}
         if scale <= 24:
             g = _graph(seraph, synth, torch, scale, 256)
-            runs = ([("sssp", s) for s in (0, 12345, 99, 777, 4242, 31337)] +
-                    [("pagerank", 0), ("bfs", 0), ("bfs", 12345)])
-            x, k, p = collect(seraph, torch, g, 2 << 30, 64, runs)
+            runs = ([("sssp", s, 64, {}) for s in (0, 12345, 99, 777, 4242, 31337)] +
+                    [("pagerank", 0, 64, pr), ("bfs", 0, 64, {}), ("bfs", 12345, 64, {})])
+            x, k, p = collect(seraph, torch, g, 2 << 30, runs)
         else:
             g = _graph(seraph, synth, torch, scale, 512)
-            x, k, p = collect(seraph, torch, g, 16 << 30, 16, [("sssp", 0), ("pagerank", 0)])
+            x, k, p = collect(seraph, torch, g, 16 << 30,
+                              [("sssp", 0, 16, {}), ("pagerank", 0, 14, pr)])
         xs += x
         ks += k
         ps += p
