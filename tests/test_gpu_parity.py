@@ -218,6 +218,25 @@ def test_pagerank_ragged_vertex_counts(n):
         assert l1 <= PR_L1 and rel <= PR_REL, (n, nm, l1, rel, st)
 
 
+def test_idle_passes_only_while_a_copy_is_in_flight(r16):
+    """Idle-slot passes (Sec. 3.2) run only while the next chunk's copy is
+    pending: once every chunk is resident (after the first sweep) a step runs
+    its base passes only, so the later sweeps run exactly one pass per chunk."""
+    g = r16["g"]
+    kw = dict(window=1, slots=8, passes=1, pvu="off", budget_bytes=8 * (slot_bytes(g, False) + 256))
+    x, st = seraph.run(g, "pagerank", max_passes=6, **kw)
+    assert st["resident"] == 1 and st["converged"] == 1
+    C, S = st["chunks"], st["sweeps"]
+    later = (S - 1) * C                       # steps after the first sweep: one pass each
+    assert C + later <= st["passes_run"] + st["passes_skipped"] <= 6 * C + later, st
+    l1, rel = pr_errors(x, r16["pr"])
+    assert l1 <= PR_L1 and rel <= PR_REL
+    d, st2 = seraph.run(g, "sssp", source=0, max_passes=6,
+                        **dict(kw, budget_bytes=8 * (slot_bytes(g, True) + 512)))
+    assert st2["resident"] == 1 and np.array_equal(d, r16["sssp"])
+    assert st2["passes_run"] + st2["passes_skipped"] <= 6 * st2["chunks"] + (st2["sweeps"] - 1) * st2["chunks"]
+
+
 def test_pagerank_is_deterministic(r16):
     a, _ = seraph.run(r16["g"], "pagerank", **cfg1(r16["g"], False))
     b, _ = seraph.run(r16["g"], "pagerank", **cfg1(r16["g"], False))
