@@ -64,8 +64,8 @@ def parse():
     ap.add_argument("--no-paper-schedule", action="store_true")
     ap.add_argument("--ablation", action="store_true",
                     help="also run the paper's ablation ladder (Fig. 9 style) on the same graph: "
-                         "baseline, pipelined subgraph iteration, + predictive updating, + this "
-                         "build's residency/packing")
+                         "baseline, pipelined subgraph iteration, + predictive updating, + the "
+                         "library's resident chunks, packed pages and PageRank accelerations")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-scheduler comparison run")
     ap.add_argument("--workload", default="streamed", choices=["streamed", "batch"],
@@ -546,8 +546,9 @@ def main():
         # baseline: one pass per streamed page pair (double buffer, no reuse), no prediction;
         # psi: k = 4 local passes over a window of 4 chunks while the next streams (Fig. 4);
         # psi+pvu: with the predictive vertex update (strong for SSSP, weak for PageRank);
-        # then this build's schedule without and with packed SSSP pages, hybrid pages, and
-        # PageRank's unit-sum scaling at sweep ends (off in every row before the last).
+        # then the library's resident-chunk schedule without and with packed SSSP pages,
+        # hybrid pages, PageRank's unit-sum scaling at sweep ends and its over-relaxation
+        # (the scaling only in the last two rows, the over-relaxation only in the last).
         ladder = [
             ("baseline", dict(order="cyclic", window=1, slots=2, pvu="off", columns="plain"),
              dict(order="cyclic", window=1, slots=2, pvu="off", columns="plain")),
