@@ -461,11 +461,15 @@ typedef struct seraph_batch_params {
     uint32_t use_graph;         /* 1: capture the launch in a CUDA graph      */
     uint32_t replays;           /* timed repetitions (>= 1)                   */
     uint32_t timeout_ms;        /* bound on every wait, device and host       */
-    uint32_t delta;             /* SSSP near-far bucket width (0 = 64): an
-                                   improved vertex whose distance is below the
-                                   current split joins the next round, the
-                                   rest wait in a far pile until the split
-                                   rises by delta; BFS ignores it            */
+    uint32_t delta;             /* SSSP near-far bucket width: an improved
+                                   vertex whose distance is below the current
+                                   split joins the next round, the rest wait
+                                   in a far pile until the split rises by
+                                   delta; BFS ignores it.  0 = per graph: with
+                                   mapping AUTO the autotuner times 64, 128,
+                                   256 and 512 on the graph's SSSP queries and
+                                   keeps the fastest (cached with the
+                                   mapping), otherwise 64                    */
     void*    stream;            /* cudaStream_t, NULL = own                   */
     uint32_t bfs_pull_div;      /* BFS direction switch (Beamer et al.): a
                                    round whose frontier exceeds n / div runs

@@ -755,7 +755,9 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
     SR_CHECK(out_mem == SERAPH_MEM_HOST || out_mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad out_mem");
     SR_CHECK(P->mapping >= SERAPH_MAP_AUTO && P->mapping <= SERAPH_MAP_CTA, SERAPH_EINVAL, "bad mapping");
     SR_CHECK(P->tile == 0 || (P->tile <= (1u << 20)), SERAPH_EINVAL, "bad tile");
+    // 0 = a width per graph (tuned below with the mapping), else the caller's
     const uint32_t delta = P->delta ? P->delta : kDefaultDelta;
+    const bool tune_delta = P->delta == 0 && P->mapping == SERAPH_MAP_AUTO;
     const uint32_t pull_div = P->bfs_pull_div ? P->bfs_pull_div : kDefaultPullDiv;
     std::vector<seraph_bgraph*> graphs(graphs_in, graphs_in + ng);
     for (auto* g : graphs) SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
@@ -765,7 +767,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
     seraph_batch_stats S{};
     auto t_tune = std::chrono::steady_clock::now();
     // per-graph mapping and tile: fixed, cached, or autotuned on the graph's own queries
-    std::vector<uint32_t> gmap(ng), gtile(ng);
+    std::vector<uint32_t> gmap(ng), gtile(ng), gdelta(ng, delta);
     for (uint32_t gi = 0; gi < ng; ++gi) {
         if (P->mapping != SERAPH_MAP_AUTO) {
             gmap[gi] = (uint32_t)P->mapping;
@@ -775,6 +777,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
         if (graphs[gi]->tuned_mapping) {
             gmap[gi] = graphs[gi]->tuned_mapping;
             gtile[gi] = graphs[gi]->tuned_tile;
+            if (tune_delta && graphs[gi]->tuned_delta) gdelta[gi] = graphs[gi]->tuned_delta;
             continue;
         }
         std::vector<QSpec> sub;
@@ -793,10 +796,26 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
                     if (o.ms < best) { best = o.ms; bm = mp; bt = tl; }
                 }
         }
+        // the near-far width for this graph's SSSP queries, with the chosen mapping
+        uint32_t bd = delta;
+        std::vector<QSpec> ss;
+        for (const QSpec& x : sub)
+            if (x.algo == SERAPH_SSSP && graphs[gi]->weighted) ss.push_back(x);
+        if (tune_delta && !ss.empty()) {
+            float bestd = 1e30f;
+            for (uint32_t d : {64u, 128u, 256u, 512u}) {
+                for (auto& x : ss) { x.mapping = bm; x.tile = bt; x.delta = d; }
+                std::vector<DevBuf<uint32_t>> hold;
+                const Outcome o = launch_batch(one, ss, false, 2, P->timeout_ms, s.s, nullptr, &hold);
+                if (o.ms < bestd) { bestd = o.ms; bd = d; }
+            }
+        }
         graphs[gi]->tuned_mapping = (int)bm;
         graphs[gi]->tuned_tile = bt;
+        graphs[gi]->tuned_delta = tune_delta && !ss.empty() ? bd : 0;
         gmap[gi] = bm;
         gtile[gi] = bt;
+        gdelta[gi] = bd;
     }
     S.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_tune).count();
 
@@ -811,7 +830,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
         uint32_t tile = gtile[Q.graph];
         if (gmap[Q.graph] == SERAPH_MAP_CTA) tile = std::min<uint32_t>(tile, kMaxCtaTile);
         qs[q] = QSpec{Q.graph, algo, Q.source, gmap[Q.graph], tile,
-                      out_mem == SERAPH_MEM_DEVICE ? Q.out : nullptr, delta, pull_div};
+                      out_mem == SERAPH_MEM_DEVICE ? Q.out : nullptr, gdelta[Q.graph], pull_div};
     }
     std::vector<uint32_t*> dist(nq);
     std::vector<DevBuf<uint32_t>> hold;

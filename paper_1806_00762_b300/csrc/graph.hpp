@@ -111,4 +111,5 @@ struct seraph_bgraph {
     seraph::Adjacency in_adj;     // rows = destinations (bottom-up BFS rounds), no weights
     int tuned_mapping = 0;        // 0: not tuned yet
     uint32_t tuned_tile = 0;
+    uint32_t tuned_delta = 0;     // SSSP near-far width chosen with the mapping (0: none)
 };
