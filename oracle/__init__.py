@@ -9,6 +9,9 @@ The C part (``oracle.c``) writes out the plain definitions: Dijkstra, FIFO
 BFS, union-find weakly-connected components and FP64 PageRank power iteration
 (evaluation section "Graph Algorithms"; Sec. 4.3 for PageRank), the CSR/CSC
 build and the destination-range page cut (Sec. 3.1 "Subgraph Organization"),
+the FP64 PageRank step certificate over a replayed raw edge stream
+(``pagerank_step_edges``: one map application for graphs too large for one
+CSR build, whose residual bounds the L1 distance to the fixpoint),
 the out-degree vertex order (``degree_order``; a layout outside the paper
 that renames vertices only) and the packed page columns (``pack_gaps``;
 LEB128 gaps, a lossless encoding outside the paper).
@@ -77,6 +80,11 @@ def _L():
                                     ctypes.POINTER(c_dbl)]
     lib.oracle_pagerank_apply.restype = None
     lib.oracle_pagerank_apply.argtypes = [c_u64, _u64p, _u32p, c_dbl, _f64p, _f64p]
+    lib.oracle_pr_bucket_keys.restype = c_u64
+    lib.oracle_pr_bucket_keys.argtypes = [c_u64, _u32p, _u32p, c_u32, c_u32, _u64p, c_u64, c_u64]
+    lib.oracle_pr_bucket_apply.restype = c_u64
+    lib.oracle_pr_bucket_apply.argtypes = [c_u64, _u64p, _u64p, c_u32, c_int, _u32p, c_u64, c_u32,
+                                           vp, vp]
     lib.oracle_sp_check_edges.restype = c_u64
     lib.oracle_sp_check_edges.argtypes = [c_u64, _u32p, _u32p, vp, _u32p, _u8p]
     lib.oracle_sp_check_tight.restype = c_u64
@@ -267,6 +275,54 @@ def pagerank_apply(g: CSR, x: np.ndarray, d: float = 0.85) -> np.ndarray:
     _L().oracle_pagerank_apply(g.n, g.row_off, g.col, d,
                                np.ascontiguousarray(x, dtype=np.float64), y)
     return y
+
+
+def pagerank_step_edges(n: int, edge_chunks, x, d: float = 0.85, nbuckets: int = 4,
+                        nsub: int = 256, cap: int | None = None, m_hint: int | None = None):
+    """One FP64 PageRank map application T(x) (same definition as
+    ``pagerank_apply``) over a raw edge stream, for graphs too large to build
+    as one CSR; ``x`` may also hold several vectors as the rows of an (nx, n)
+    array, each mapped in the same rounds.  ``edge_chunks()`` must return a fresh iterator of (src, dst)
+    uint32 chunks of the raw edges (self-loops and duplicates as drawn); it is
+    replayed 2 * nbuckets times: one round over the destination classes for
+    the kept out-degrees, one for the pull sums.  Returns (T(x), distinct
+    edge count).  ``cap`` bounds the keys held at once (default 1.25 m /
+    nbuckets + 2^20 with ``m_hint`` raw edges).
+
+    ||x - x*||_1 <= ||T(x) - x||_1 / (1 - d) for every x (T is a
+    d-contraction in L1), which makes this a certificate of a claimed
+    fixpoint without computing the fixpoint."""
+    L = _L()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    single = x.ndim == 1
+    x = x.reshape(-1, n)
+    nx = x.shape[0]
+    if cap is None:
+        if m_hint is None:
+            raise ValueError("give cap or m_hint")
+        cap = int(1.25 * m_hint / nbuckets) + (1 << 20)
+    keys = np.empty(cap, dtype=np.uint64)
+    tmp = np.empty(cap, dtype=np.uint64)
+    outdeg = np.zeros(n, dtype=np.uint32)
+    s = np.zeros((nx, n), dtype=np.float64)
+    distinct = 0
+    for mode in (0, 1):
+        for b in range(nbuckets):
+            k = 0
+            for src, dst in edge_chunks():
+                src, dst = _u32(src), _u32(dst)
+                k = int(L.oracle_pr_bucket_keys(src.shape[0], src, dst, b, nbuckets, keys, k, cap))
+                if k == (1 << 64) - 1:
+                    raise MemoryError("destination class larger than cap")
+            cnt = int(L.oracle_pr_bucket_apply(k, keys, tmp, nsub, mode, outdeg, n, nx,
+                                               x.ctypes.data if mode else None,
+                                               s.ctypes.data if mode else None))
+            if mode == 0:
+                distinct += cnt
+    del keys, tmp
+    dangling = x[:, outdeg == 0].sum(axis=1)
+    y = (1.0 - d) / n + d * (s + dangling[:, None] / n)
+    return (y[0] if single else y), distinct
 
 
 def sp_check_edges(src, dst, w, dist, tight) -> int:

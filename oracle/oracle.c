@@ -10,6 +10,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------- graph */
 
@@ -333,4 +336,98 @@ uint64_t oracle_sp_check_tight(uint64_t n, uint32_t source, const uint32_t* dist
     for (uint64_t v = 0; v < n; ++v)
         if (v != source && dist[v] != ORACLE_INF && !tight[v]) bad += 1;
     return bad;
+}
+
+/* ------------------------------------------- PageRank step certificate */
+
+/* Destination hash shared by the two levels of the certificate's partition
+ * (Knuth's multiplicative hashing with the 32-bit golden-ratio constant). */
+static uint32_t pr_dst_hash(uint32_t v) { return v * 0x9E3779B1u; }
+
+static uint32_t pr_bucket_of(uint32_t v, uint32_t nbuckets)
+{
+    return (uint32_t)(((uint64_t)pr_dst_hash(v) * nbuckets) >> 32);
+}
+
+uint64_t oracle_pr_bucket_keys(uint64_t count, const uint32_t* src, const uint32_t* dst,
+                               uint32_t bucket, uint32_t nbuckets, uint64_t* keys, uint64_t at,
+                               uint64_t cap)
+{
+    uint64_t cnt[257];
+    int nt_used = 1;
+    int over = 0;
+    int want = 1;
+#ifdef _OPENMP
+    want = omp_get_max_threads() < 256 ? omp_get_max_threads() : 256;
+#endif
+    memset(cnt, 0, sizeof(cnt));
+    #pragma omp parallel num_threads(want)
+    {
+        int t = 0, nt = 1;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+        nt = omp_get_num_threads();
+#endif
+        uint64_t lo = count * (uint64_t)t / (uint64_t)nt, hi = count * (uint64_t)(t + 1) / (uint64_t)nt;
+        uint64_t c = 0;
+        for (uint64_t i = lo; i < hi; ++i)
+            if (src[i] != dst[i] && pr_bucket_of(dst[i], nbuckets) == bucket) ++c;
+        cnt[t + 1] = c;
+        #pragma omp barrier
+        #pragma omp single
+        {
+            nt_used = nt;
+            for (int j = 0; j < nt; ++j) cnt[j + 1] += cnt[j];
+            over = at + cnt[nt] > cap;
+        }
+        if (!over) {
+            uint64_t o = at + cnt[t];
+            for (uint64_t i = lo; i < hi; ++i)
+                if (src[i] != dst[i] && pr_bucket_of(dst[i], nbuckets) == bucket)
+                    keys[o++] = ((uint64_t)dst[i] << 32) | src[i];
+        }
+    }
+    return over ? UINT64_MAX : at + cnt[nt_used];
+}
+
+static int cmp_u64(const void* pa, const void* pb)
+{
+    uint64_t a = *(const uint64_t*)pa, b = *(const uint64_t*)pb;
+    return a < b ? -1 : (a > b);
+}
+
+uint64_t oracle_pr_bucket_apply(uint64_t k, uint64_t* keys, uint64_t* tmp, uint32_t nsub, int mode,
+                                uint32_t* outdeg, uint64_t n, uint32_t nx, const double* x, double* s)
+{
+    /* split by a second hash level so that each destination lands in one
+     * part (mode 1 sums without races), then sort each part */
+    uint64_t* start = (uint64_t*)calloc((size_t)nsub + 1, sizeof(uint64_t));
+    for (uint64_t i = 0; i < k; ++i) start[((pr_dst_hash((uint32_t)(keys[i] >> 32)) >> 8) % nsub) + 1] += 1;
+    for (uint32_t p = 0; p < nsub; ++p) start[p + 1] += start[p];
+    uint64_t* fill = (uint64_t*)malloc((size_t)nsub * sizeof(uint64_t));
+    memcpy(fill, start, (size_t)nsub * sizeof(uint64_t));
+    for (uint64_t i = 0; i < k; ++i)
+        tmp[fill[(pr_dst_hash((uint32_t)(keys[i] >> 32)) >> 8) % nsub]++] = keys[i];
+    free(fill);
+    uint64_t distinct = 0;
+    #pragma omp parallel for schedule(dynamic, 1) reduction(+ : distinct)
+    for (int64_t p = 0; p < (int64_t)nsub; ++p) {
+        uint64_t* a = tmp + start[p];
+        uint64_t len = start[p + 1] - start[p];
+        qsort(a, len, sizeof(uint64_t), cmp_u64);
+        for (uint64_t i = 0; i < len; ++i) {
+            if (i > 0 && a[i] == a[i - 1]) continue;      /* duplicate edge */
+            uint32_t u = (uint32_t)a[i], v = (uint32_t)(a[i] >> 32);
+            ++distinct;
+            if (mode == 0) {
+                #pragma omp atomic
+                outdeg[u] += 1;
+            } else {
+                for (uint32_t j = 0; j < nx; ++j)
+                    s[j * n + v] += x[j * n + u] / (double)outdeg[u];
+            }
+        }
+    }
+    free(start);
+    return distinct;
 }

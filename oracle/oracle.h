@@ -71,6 +71,34 @@ int oracle_pagerank(uint64_t n, const uint64_t* row_off, const uint32_t* col, do
 void oracle_pagerank_apply(uint64_t n, const uint64_t* row_off, const uint32_t* col, double d,
                            const double* x, double* y);
 
+/* FP64 PageRank step certificate for graphs too large for one CSR build.
+ *
+ * One map application T(x)_v = (1-d)/n + d (sum_{u->v} x_u/outdeg(u) + D/n)
+ * (the PageRank definition above) is assembled from a raw edge stream that
+ * the caller replays, bucket by bucket: destinations are split into
+ * `nbuckets` classes by a multiplicative hash, and for each class the caller
+ * streams every raw edge through oracle_pr_bucket_keys, which keeps the keys
+ * (dst << 32 | src) of the class's edges (self-loops dropped) in
+ * keys[at..]; cap bounds the buffer (returns UINT64_MAX when it would
+ * overflow, else the new key count).  oracle_pr_bucket_apply then sorts the
+ * keys (in `nsub` parts split by the same hash, tmp = scratch of k entries),
+ * drops duplicate edges and, for every distinct edge (u, v),
+ *   mode 0: outdeg[u] += 1 (a first round over all classes gives the kept
+ *           out-degrees),
+ *   mode 1: s[j n + v] += x[j n + u] / outdeg[u] for each of the nx
+ *           vectors x (rows of n), each destination's in-edges added in
+ *           ascending source order (a second round gives the pull sums).
+ * Returns the number of distinct edges of the class.  The caller forms
+ * T(x) from s, the dangling mass D and d.  Since T is an affine map whose
+ * linear part is d times a column-stochastic matrix, ||T x - T y||_1 <=
+ * d ||x - y||_1, so ||x - x*||_1 <= ||T x - x||_1 / (1 - d) for any x: the
+ * step residual bounds the distance to the fixpoint. */
+uint64_t oracle_pr_bucket_keys(uint64_t count, const uint32_t* src, const uint32_t* dst,
+                               uint32_t bucket, uint32_t nbuckets, uint64_t* keys, uint64_t at,
+                               uint64_t cap);
+uint64_t oracle_pr_bucket_apply(uint64_t k, uint64_t* keys, uint64_t* tmp, uint32_t nsub, int mode,
+                                uint32_t* outdeg, uint64_t n, uint32_t nx, const double* x, double* s);
+
 /* SSSP/BFS certificate over a stream of raw edges (self-loops ignored; w may
  * be NULL for unit weights).  Counts edges with dist[v] > dist[u] + w (the
  * triangle inequality violated) and marks tight[v] = 1 when

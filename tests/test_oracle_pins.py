@@ -379,3 +379,88 @@ def test_pagerank_apply_fixpoint_and_contraction():
     y1 = oracle.pagerank_apply(g, y0)
     # L1 contraction by d on probability vectors
     assert np.abs(oracle.pagerank_apply(g, y1) - y1).sum() <= D * np.abs(y1 - y0).sum() + 1e-15
+
+
+# ------------------------------------------- PageRank step certificate
+
+def pr_dense_map(n, src, dst, x, d=D):
+    """T(x) = (1-d)/n + d A x with the same dense A as pr_dense_solve."""
+    adj = np.zeros((n, n))
+    for u, v in zip(src, dst):
+        if u != v:
+            adj[u, v] = 1.0
+    out = adj.sum(1)
+    A = np.where(out[None, :] > 0, adj.T / np.maximum(out, 1)[None, :], 1.0 / n)
+    return (1 - d) / n + d * (A @ x)
+
+
+def _chunks(src, dst, size):
+    def it():
+        for e0 in range(0, len(src), size):
+            yield src[e0:e0 + size], dst[e0:e0 + size]
+    return it
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pagerank_step_edges_vs_dense_map(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(1, 65))
+    src, dst, _ = graphs.random_graph(n, int(rng.integers(0, 3 * n + 1)), seed=seed)
+    x = rng.random(n)
+    y, E = oracle.pagerank_step_edges(n, _chunks(src, dst, 7), x, nbuckets=int(rng.integers(1, 5)),
+                                      nsub=int(rng.integers(1, 9)), m_hint=max(len(src), 1))
+    assert np.allclose(y, pr_dense_map(n, src, dst, x), rtol=1e-13, atol=1e-16)
+    assert E == len({(int(u), int(v)) for u, v in zip(src, dst) if u != v})
+
+
+@pytest.mark.parametrize("nb,nsub", [(1, 1), (3, 7), (8, 256)])
+def test_pagerank_step_edges_matches_csr_map_on_rmat(nb, nsub):
+    n = 1 << 12
+    src, dst = synth.rmat_edges(12)
+    g = oracle.build_csr(n, src, dst)
+    x = np.random.default_rng(nb).random(n)
+    y, E = oracle.pagerank_step_edges(n, _chunks(src, dst, 10007), x, nbuckets=nb, nsub=nsub,
+                                      m_hint=len(src))
+    assert E == g.m
+    assert np.allclose(y, oracle.pagerank_apply(g, x), rtol=1e-14, atol=0)
+
+
+def test_pagerank_step_certificate_bounds_the_error():
+    n = 1 << 11
+    src, dst = synth.rmat_edges(11)
+    g = oracle.build_csr(n, src, dst)
+    xs, _, _ = oracle.pagerank(g)
+    it = _chunks(src, dst, 1 << 14)
+    y, _ = oracle.pagerank_step_edges(n, it, xs, nbuckets=2, m_hint=len(src))
+    assert np.abs(y - xs).sum() < 1e-14
+    rng = np.random.default_rng(5)
+    for scale in (1e-3, 1e-6):
+        x = xs + scale * rng.standard_normal(n) / n
+        y, _ = oracle.pagerank_step_edges(n, it, x, nbuckets=2, m_hint=len(src))
+        r = np.abs(y - x).sum()
+        # (1 - d) ||x - x*||_1 <= ||T x - x||_1 <= (1 + d) ||x - x*||_1
+        assert np.abs(x - xs).sum() <= r / (1 - D) * (1 + 1e-9)
+        assert r <= (1 + D) * np.abs(x - xs).sum() * (1 + 1e-9)
+    # one vertex off by delta: (1-d)|delta| <= residual <= (1+d)|delta|
+    for v in (0, 17, n - 1):
+        x = xs.copy()
+        x[v] += 1e-4
+        y, _ = oracle.pagerank_step_edges(n, it, x, nbuckets=3, m_hint=len(src))
+        r = np.abs(y - x).sum()
+        assert (1 - D) * 1e-4 * (1 - 1e-9) <= r <= (1 + D) * 1e-4 * (1 + 1e-9)
+
+
+def test_pagerank_step_edges_rejects_a_too_small_buffer():
+    src, dst = synth.rmat_edges(10)
+    with pytest.raises(MemoryError):
+        oracle.pagerank_step_edges(1 << 10, _chunks(src, dst, 4096), np.ones(1 << 10), cap=100)
+
+
+def test_pagerank_step_edges_maps_several_vectors_at_once():
+    n = 1 << 10
+    src, dst = synth.rmat_edges(10)
+    g = oracle.build_csr(n, src, dst)
+    X = np.random.default_rng(3).random((3, n))
+    Y, _ = oracle.pagerank_step_edges(n, _chunks(src, dst, 5000), X, nbuckets=2, m_hint=len(src))
+    for j in range(3):
+        assert np.allclose(Y[j], oracle.pagerank_apply(g, X[j]), rtol=1e-14, atol=0)
