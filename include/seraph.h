@@ -86,6 +86,13 @@ enum seraph_order { SERAPH_ORDER_CYCLIC = 0, SERAPH_ORDER_ZIGZAG = 1 };
                                  streams ~2 bytes per edge instead of 4; runs
                                  pick the form with seraph_params.columns    */
 
+#define SERAPH_OUT_EDGES  8u  /* also keep the kept edges as an out-edge CSR in
+                                 pinned host memory (u64 offsets per source,
+                                 u32 destinations ascending, weights in the
+                                 stored width), read directly by the GPU over
+                                 the host link: the push stage of sparse
+                                 sweeps (seraph_params.push) needs it        */
+
 typedef struct seraph_graph seraph_graph;  /* opaque, library-owned */
 
 typedef struct seraph_graph_info {
@@ -109,6 +116,8 @@ typedef struct seraph_graph_info {
     uint64_t packed_bytes;      /* pinned bytes of all packed page structures */
     uint64_t packed_data_bytes; /* gap-stream bytes of all pages (unpadded)  */
     uint64_t max_page_packed_bytes;
+    uint64_t out_edge_bytes;    /* pinned bytes of the out-edge CSR (0 without
+                                   SERAPH_OUT_EDGES)                         */
 } seraph_graph_info;
 
 /*
@@ -133,7 +142,10 @@ int seraph_graph_from_edges(uint64_t n, uint64_t m, const uint32_t* src, const u
                             void* stream, seraph_graph** out);
 
 /* Same, from a CSR (row_off: n+1 uint64 offsets; col: row_off[n] ids; w NULL
- * or row_off[n] weights), all in `mem`. */
+ * or row_off[n] weights), all in `mem`.  row_off must start at 0 and never
+ * decrease (SERAPH_EINVAL otherwise; offsets in host memory are checked
+ * before any device call, offsets in device memory by a kernel before they
+ * are used). */
 int seraph_graph_from_csr(uint64_t n, const uint64_t* row_off, const uint32_t* col,
                           const uint32_t* w, int mem, uint32_t flags, uint32_t num_pages,
                           void* stream, seraph_graph** out);
@@ -160,6 +172,12 @@ int  seraph_graph_export_perm(const seraph_graph* g, uint32_t* perm);
  * pages concatenated without padding: boff[n+1] global byte offsets of each
  * destination's bytes, data[packed_data_bytes].  Either may be NULL. */
 int  seraph_graph_export_packed(const seraph_graph* g, uint64_t* boff, uint8_t* data);
+
+/* The out-edge CSR (SERAPH_OUT_EDGES graphs; SERAPH_EINVAL otherwise), in
+ * internal ids: out_off[n+1], out_col[m] (destinations ascending per
+ * source), out_w[m] weights (may be NULL; ignored for unweighted graphs). */
+int  seraph_graph_export_out_edges(const seraph_graph* g, uint64_t* out_off, uint32_t* out_col,
+                                   uint32_t* out_w);
 
 /* A run keeps its device buffers (edge ring, vertex arrays, lists) with the
  * graph for the next run, so repeated runs allocate nothing; this returns
@@ -271,6 +289,22 @@ typedef struct seraph_params {
                                    changes x by less than pr_pvu_off_below
                                    (L1); later sweeps publish x_new.  0 or 1
                                    = plain updates; must lie in [0, 2)     */
+    uint32_t push;              /* dense -> sparse switch (Sec. 3.1, the
+                                   heterogeneous execution model: sparse
+                                   iterations push from the active vertices):
+                                   1 = after a sweep in which every
+                                   non-final vertex was relaxed (prediction
+                                   off, or strong) and at most push_below
+                                   vertices changed, the run leaves the pages
+                                   and pushes from the changed vertices over
+                                   the graph's out-edge CSR (SERAPH_OUT_EDGES),
+                                   round by round on the GPU, until a round
+                                   changes nothing: the fixpoint.  SSSP, BFS
+                                   and CC (on a symmetrized graph); fixed
+                                   schedules only.  0 = off                  */
+    uint32_t pad2;
+    uint64_t push_below;        /* switch threshold in changed vertices (0 =
+                                   n / 256)                                  */
 } seraph_params;
 
 #define SERAPH_L2_HOT_AUTO UINT64_MAX
@@ -303,6 +337,13 @@ typedef struct seraph_stats {
     double   relax_ms;          /* sum of relax-kernel durations (events)     */
     uint64_t relax_launches;    /* relax kernels launched                     */
     uint64_t kernel_launches;   /* all library kernels launched by the run    */
+    uint64_t packed_edges;      /* part of edges_relaxed read from packed pages */
+    uint64_t code_bytes;        /* their LEB128 code bytes (the column bytes a
+                                   relax pass reads for them, against 4 per
+                                   edge on plain pages)                       */
+    uint64_t push_edges;        /* out-edges read by the push stage           */
+    uint32_t push_rounds;       /* push rounds with a non-empty frontier      */
+    uint32_t push_sweep;        /* sweeps run before the switch (0: none)     */
 } seraph_stats;
 
 int seraph_params_default(seraph_params* p, int algo);
@@ -336,8 +377,12 @@ int seraph_run(seraph_graph* g, const seraph_params* p, void* out_values, int ou
  * unit weights) are caller-owned device arrays; values[n] receives the
  * distances / levels / labels (caller-owned device array); passes_out (host,
  * may be NULL) receives the number of passes.  For CC pass the symmetric
- * graph.  Errors: SERAPH_EINVAL (n > SERAPH_NOALLOC_MAX_VERTICES, bad algo,
- * NULL pointers, source >= n), SERAPH_EOVERFLOW, SERAPH_ECUDA.
+ * graph.  Before anything else is read through the CSC a kernel checks it:
+ * col_off must start at 0 and never decrease and every row id must be < n
+ * (SERAPH_EINVAL otherwise, values untouched); row must hold col_off[n]
+ * entries (and w, when given, as many), which no call can check.  Errors:
+ * SERAPH_EINVAL (n > SERAPH_NOALLOC_MAX_VERTICES, bad algo, NULL pointers,
+ * source >= n, the CSC check above), SERAPH_EOVERFLOW, SERAPH_ECUDA.
  *
  * The first call on each device resolves the scratch array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
@@ -502,6 +547,23 @@ int  seraph_batch_params_default(seraph_batch_params* p);
 int  seraph_batch_run(seraph_bgraph* const* graphs, uint32_t ng, const seraph_query* queries,
                       uint32_t nq, int out_mem, const seraph_batch_params* p,
                       seraph_batch_stats* stats);
+
+/*
+ * Host-side fault injection and accounting, for tests of the failure paths
+ * (not in the paper).  Every failure is made on the host; nothing here makes
+ * the device fault or wait.
+ *
+ * seraph_debug_fail_pinned_alloc(k): the k-th pinned host allocation the
+ * library makes from now on (k >= 1; process-wide, any thread) fails as if
+ * the host had no pinned memory left, and the call that made it returns
+ * SERAPH_ENOMEM after freeing what it had taken.  k = 0 disarms.  Returns
+ * SERAPH_OK.
+ * seraph_debug_pinned_bytes(): pinned host bytes the library holds right now
+ * (all graphs, runs and buffers of the process), so that a test can check
+ * that a failed call gave back everything it allocated.
+ */
+int      seraph_debug_fail_pinned_alloc(uint32_t k);
+uint64_t seraph_debug_pinned_bytes(void);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* seraph_last_error(void);

@@ -52,9 +52,9 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
-def _flags(symmetrize: bool, reorder: bool, compress: bool = False) -> int:
+def _flags(symmetrize: bool, reorder: bool, compress: bool = False, out_edges: bool = False) -> int:
     return ((C.SYMMETRIZE if symmetrize else 0) | (C.REORDER if reorder else 0) |
-            (C.COMPRESS if compress else 0))
+            (C.COMPRESS if compress else 0) | (C.OUT_EDGES if out_edges else 0))
 
 
 class Graph:
@@ -65,7 +65,7 @@ class Graph:
 
     @classmethod
     def from_edges(cls, n, src, dst, w=None, symmetrize=False, num_pages=1, stream=None,
-                   reorder=False, compress=False):
+                   reorder=False, compress=False, out_edges=False):
         ps, ms, ks = _ptr_mem(src)
         pd, md, kd = _ptr_mem(dst)
         pw, mw, kw = _ptr_mem(w)
@@ -79,19 +79,19 @@ class Graph:
                 raise TypeError("edge arrays must hold 32-bit unsigned integers")
         out = ctypes.c_void_p()
         C.check(C.lib().seraph_graph_from_edges(n, m, ps, pd, pw, ms,
-                                                _flags(symmetrize, reorder, compress),
+                                                _flags(symmetrize, reorder, compress, out_edges),
                                                 num_pages, _stream_ptr(stream), ctypes.byref(out)))
         return cls(out.value)
 
     @classmethod
     def from_csr(cls, n, row_off, col, w=None, symmetrize=False, num_pages=1, stream=None,
-                 reorder=False, compress=False):
+                 reorder=False, compress=False, out_edges=False):
         pr, mr, kr = _ptr_mem(row_off)
         pc, mc, kc = _ptr_mem(col)
         pw, mw, kw = _ptr_mem(w)
         out = ctypes.c_void_p()
         C.check(C.lib().seraph_graph_from_csr(n, pr, pc, pw, mr,
-                                              _flags(symmetrize, reorder, compress),
+                                              _flags(symmetrize, reorder, compress, out_edges),
                                               num_pages, _stream_ptr(stream), ctypes.byref(out)))
         return cls(out.value)
 
@@ -124,6 +124,17 @@ class Graph:
         data = np.empty(max(i["packed_data_bytes"], 1), dtype=np.uint8)
         C.check(C.lib().seraph_graph_export_packed(self._h, boff.ctypes.data, data.ctypes.data))
         return boff, data[:i["packed_data_bytes"]]
+
+    def export_out_edges(self):
+        """(out_off[n+1], out_col, out_w or None) of an out_edges=True graph,
+        in internal ids."""
+        i = self.info()
+        off = np.empty(i["n"] + 1, dtype=np.uint64)
+        col = np.empty(max(i["m"], 1), dtype=np.uint32)
+        w = np.empty(max(i["m"], 1), dtype=np.uint32) if i["weighted"] else None
+        C.check(C.lib().seraph_graph_export_out_edges(self._h, off.ctypes.data, col.ctypes.data,
+                                                      None if w is None else w.ctypes.data))
+        return off, col[:i["m"]], (None if w is None else w[:i["m"]])
 
     def release_buffers(self) -> None:
         """Give back the device buffers that runs keep with the graph."""
@@ -280,6 +291,17 @@ def run(graph: Graph, algo, out=None, stream=None, **kw):
     st = C.Stats()
     C.check(C.lib().seraph_run(graph._h, ctypes.byref(p), po, mo, ctypes.byref(st)))
     return out, st.as_dict()
+
+
+def debug_fail_pinned_alloc(k: int) -> None:
+    """Make the k-th pinned host allocation from now fail (0 = off); a test
+    hook for the ENOMEM path (seraph_debug_fail_pinned_alloc)."""
+    C.check(C.lib().seraph_debug_fail_pinned_alloc(int(k)))
+
+
+def debug_pinned_bytes() -> int:
+    """Pinned host bytes the library holds (seraph_debug_pinned_bytes)."""
+    return int(C.lib().seraph_debug_pinned_bytes())
 
 
 def gather_probe(n_values, n_gathers, hot_values, hot_frac=1.0, reps=5, stream=None) -> float:

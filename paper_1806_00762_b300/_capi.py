@@ -37,6 +37,7 @@ ORDERS = {"cyclic": ORDER_CYCLIC, "zigzag": ORDER_ZIGZAG}
 SYMMETRIZE = 1
 REORDER = 2
 COMPRESS = 4
+OUT_EDGES = 8
 COLUMNS = {"auto": 0, "plain": 1, "packed": 2, "hybrid": 3}
 NOALLOC_MAX_VERTICES = 1 << 20
 INF = 0xFFFFFFFF
@@ -51,7 +52,8 @@ class GraphInfo(ctypes.Structure):
                 ("max_page_weight_bytes", u64), ("num_pages", u32), ("weighted", u32),
                 ("symmetrized", u32), ("max_in_degree", u32), ("weight_width", u32),
                 ("reordered", u32), ("packed", u32), ("reserved", u32), ("packed_bytes", u64),
-                ("packed_data_bytes", u64), ("max_page_packed_bytes", u64)]
+                ("packed_data_bytes", u64), ("max_page_packed_bytes", u64),
+                ("out_edge_bytes", u64)]
 
 
 class Params(ctypes.Structure):
@@ -64,7 +66,8 @@ class Params(ctypes.Structure):
                 ("max_passes", u32), ("slots", u32), ("group4_max_deg", u32),
                 ("group8_max_deg", u32),
                 ("sched_model", vp), ("stream", vp), ("trace", vp), ("columns", u32),
-                ("pad1", u32), ("l2_hot_bytes", u64), ("pr_omega", dbl)]
+                ("pad1", u32), ("l2_hot_bytes", u64), ("pr_omega", dbl), ("push", u32),
+                ("pad2", u32), ("push_below", u64)]
 
 
 class Stats(ctypes.Structure):
@@ -73,7 +76,9 @@ class Stats(ctypes.Structure):
                 ("bytes_streamed", u64), ("edges_relaxed", u64), ("vertices_attempted", u64),
                 ("vertices_skipped", u64), ("changes", u64), ("time_ms", dbl),
                 ("copy_ms", dbl), ("compute_ms", dbl), ("wall_ms", dbl), ("residual", dbl),
-                ("relax_ms", dbl), ("relax_launches", u64), ("kernel_launches", u64)]
+                ("relax_ms", dbl), ("relax_launches", u64), ("kernel_launches", u64),
+                ("packed_edges", u64), ("code_bytes", u64), ("push_edges", u64),
+                ("push_rounds", u32), ("push_sweep", u32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +120,7 @@ PROTOTYPES = {
     "seraph_graph_export_csc": (ctypes.c_int, [vp, vp, vp, vp, vp]),
     "seraph_graph_export_perm": (ctypes.c_int, [vp, vp]),
     "seraph_graph_export_packed": (ctypes.c_int, [vp, vp, vp]),
+    "seraph_graph_export_out_edges": (ctypes.c_int, [vp, vp, vp, vp]),
     "seraph_graph_release_buffers": (ctypes.c_int, [vp]),
     "seraph_graph_free": (None, [vp]),
     "seraph_params_default": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int]),
@@ -139,6 +145,8 @@ PROTOTYPES = {
     "seraph_batch_params_default": (ctypes.c_int, [ctypes.POINTER(BatchParams)]),
     "seraph_batch_run": (ctypes.c_int, [vp, u32, vp, u32, ctypes.c_int,
                                         ctypes.POINTER(BatchParams), ctypes.POINTER(BatchStats)]),
+    "seraph_debug_fail_pinned_alloc": (ctypes.c_int, [u32]),
+    "seraph_debug_pinned_bytes": (u64, []),
     "seraph_last_error": (ctypes.c_char_p, []),
     "seraph_version": (ctypes.c_char_p, []),
 }

@@ -1,6 +1,7 @@
 // extern "C" entry points of include/seraph.h.  Every call catches
 // exceptions, records a thread-local message and returns a SERAPH_E* code.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -48,6 +49,21 @@ int guarded(F&& f) {
 
 namespace seraph {
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+std::atomic<int64_t> g_pinned_fail_in{0};   // 0: off; k: the k-th allocation from now fails
+std::atomic<int64_t> g_pinned_bytes{0};
+}  // namespace
+
+bool take_injected_pinned_failure() {
+    int64_t k = g_pinned_fail_in.load();
+    while (k > 0) {
+        if (g_pinned_fail_in.compare_exchange_weak(k, k - 1)) return k == 1;
+    }
+    return false;
+}
+
+void note_pinned_bytes(int64_t delta) { g_pinned_bytes += delta; }
 }  // namespace seraph
 
 extern "C" {
@@ -55,6 +71,16 @@ extern "C" {
 const char* seraph_last_error(void) { return g_last_error.c_str(); }
 
 const char* seraph_version(void) { return "seraph-b300 0.1 (sm_103a)"; }
+
+int seraph_debug_fail_pinned_alloc(uint32_t k) {
+    seraph::g_pinned_fail_in.store((int64_t)k);
+    return SERAPH_OK;
+}
+
+uint64_t seraph_debug_pinned_bytes(void) {
+    const int64_t b = seraph::g_pinned_bytes.load();
+    return b > 0 ? (uint64_t)b : 0u;
+}
 
 int seraph_graph_from_edges(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
                             const uint32_t* w, int mem, uint32_t flags, uint32_t num_pages,
@@ -82,6 +108,9 @@ int seraph_graph_from_csr(uint64_t n, const uint64_t* row_off, const uint32_t* c
     return guarded([&] {
         SR_CHECK(out != nullptr, SERAPH_EINVAL, "out must not be NULL");
         *out = nullptr;
+        // host offsets are checked before any device work (device offsets by
+        // a kernel in build_graph_csr)
+        if (mem == SERAPH_MEM_HOST) seraph::check_csr_offsets_host(n, row_off);
         seraph::Stream s;
         s.use(stream);
         seraph_graph* g = new seraph_graph();
@@ -116,6 +145,7 @@ int seraph_graph_get_info(const seraph_graph* g, seraph_graph_info* info) {
         info->weight_width = g->weighted ? g->wbytes : 0;
         info->reordered = g->reordered;
         info->packed = g->packed;
+        info->out_edge_bytes = g->h_out_off.bytes + g->h_out_col.bytes + g->h_out_w.bytes;
         if (g->packed) {
             info->packed_bytes = g->h_pack.bytes;
             for (const auto& p : g->pages) {
@@ -172,6 +202,24 @@ int seraph_graph_export_packed(const seraph_graph* g, uint64_t* boff, uint8_t* d
             base += pm.pk_data;
         }
         if (boff) boff[g->n] = base;
+        return SERAPH_OK;
+    });
+}
+
+int seraph_graph_export_out_edges(const seraph_graph* g, uint64_t* out_off, uint32_t* out_col,
+                                  uint32_t* out_w) {
+    return guarded([&] {
+        SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
+        SR_CHECK(g->out_edges, SERAPH_EINVAL, "graph was built without SERAPH_OUT_EDGES");
+        if (out_off) std::memcpy(out_off, g->h_out_off.p, 8 * (g->n + 1));
+        if (out_col && g->m) std::memcpy(out_col, g->h_out_col.p, 4 * g->m);
+        if (out_w && g->weighted && g->m) {
+            for (uint64_t i = 0; i < g->m; ++i) {
+                uint32_t x = 0;
+                std::memcpy(&x, g->h_out_w.p + i * g->wbytes, g->wbytes);  // little-endian widths
+                out_w[i] = x;
+            }
+        }
         return SERAPH_OK;
     });
 }

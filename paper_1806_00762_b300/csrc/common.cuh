@@ -94,21 +94,45 @@ struct DevBuf {
     }
 };
 
+// Host-side fault injection and accounting of pinned allocations (capi.cu;
+// seraph_debug_fail_pinned_alloc / seraph_debug_pinned_bytes).
+bool take_injected_pinned_failure();
+void note_pinned_bytes(int64_t delta);
+
 // Pinned host allocation owned by the library.
 struct PinnedBuf {
     uint8_t* p = nullptr;
     size_t bytes = 0;
-    void alloc(size_t b) {
+    // mapped: also map the pages into the device address space (kernels read
+    // them directly over the host link; see device_ptr)
+    void alloc(size_t b, bool mapped = false) {
         release();
+        if (!b) return;
+        SR_CHECK(!take_injected_pinned_failure(), SERAPH_ENOMEM,
+                 "pinned host allocation failed (injected by seraph_debug_fail_pinned_alloc)");
+        SR_CUDA(cudaHostAlloc((void**)&p, b,
+                              cudaHostAllocPortable | (mapped ? cudaHostAllocMapped : 0u)));
         bytes = b;
-        if (b) SR_CUDA(cudaHostAlloc((void**)&p, b, cudaHostAllocPortable));
+        note_pinned_bytes((int64_t)b);
     }
     void release() {
-        if (p) cudaFreeHost(p);
+        if (p) {
+            cudaFreeHost(p);
+            note_pinned_bytes(-(int64_t)bytes);
+        }
         p = nullptr;
         bytes = 0;
     }
     ~PinnedBuf() { release(); }
+    // The device address of a mapped allocation (an error, not a device
+    // fault, if it is not mapped); null for an empty buffer.
+    template <class T>
+    const T* device_ptr() const {
+        if (!p) return nullptr;
+        void* d = nullptr;
+        SR_CUDA(cudaHostGetDevicePointer(&d, p, 0));
+        return (const T*)d;
+    }
 };
 
 struct Stream {

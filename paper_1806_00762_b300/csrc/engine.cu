@@ -194,7 +194,10 @@ template <int ALGO>
 __device__ __forceinline__ void finish_min(const AlgoArgs& a, uint32_t v, const MinAcc& acc,
                                            uint32_t deg, Locals& L, const Own& o) {
     bool ch = acc.best < o.old;
-    if (ch) a.val[v] = acc.best;
+    if (ch) {
+        a.val[v] = acc.best;
+        if (a.chg_stamp) a.chg_stamp[v] = a.chg_tag;
+    }
     if (ALGO == ALG_SSSP && acc.ovf && acc.best == SERAPH_INF && o.old == SERAPH_INF) L.ovf = 1;
     if (a.pvu == SERAPH_PVU_WEAK) {
         const uint8_t ns = fsm_step(a, o.st, ch);
@@ -697,6 +700,7 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
     constexpr int kWarps = kNT / 32;
     __shared__ unsigned s_cnt[kWarps][kClasses + 2];
     __shared__ unsigned s_off[kWarps][kClasses];
+    __shared__ unsigned long long s_pk[kWarps][2];
     const int par = pass & 1;
     RunState* rs = a.rs;
     if (!rs->pass_go[par]) return;
@@ -714,6 +718,7 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
     int my_cls[kCompactRounds];
     uint32_t my_p[kCompactRounds];
     unsigned n_att = 0, n_skip = 0;
+    unsigned pk_edges = 0, pk_bytes = 0;  // attempted in-edges / code bytes on packed pages
 #pragma unroll
     for (int r = 0; r < kCompactRounds; ++r) {
         my_cls[r] = -1;
@@ -739,6 +744,10 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
                     ++n_skip;
                 } else {
                     ++n_att;
+                    if (loc.boff) {
+                        pk_edges += deg;
+                        pk_bytes += loc.boff[li + 1] - loc.boff[li];
+                    }
                     my_cls[r] = deg <= a.cls_max[0] ? 0
                               : deg <= a.cls_max[1] ? 1
                               : deg <= a.cls_max[2] ? 2
@@ -761,11 +770,19 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
     }
     n_att = __reduce_add_sync(kFull, n_att);
     n_skip = __reduce_add_sync(kFull, n_skip);
+    unsigned long long pe = pk_edges, pb = pk_bytes;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pe += __shfl_xor_sync(kFull, pe, o);
+        pb += __shfl_xor_sync(kFull, pb, o);
+    }
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < kClasses; ++k) s_cnt[warp][k] = cnt[k];
         s_cnt[warp][kClasses] = n_att;
         s_cnt[warp][kClasses + 1] = n_skip;
+        s_pk[warp][0] = pe;
+        s_pk[warp][1] = pb;
     }
     __syncthreads();
     if (threadIdx.x < kClasses) {  // thread k: class k's run of the list for this block
@@ -782,6 +799,12 @@ __global__ void __launch_bounds__(kNT) compact_kernel(WindowDesc wd, AlgoArgs a,
         for (int w = 0; w < kWarps; ++w) { att += s_cnt[w][kClasses]; sk += s_cnt[w][kClasses + 1]; }
         if (att) atomicAdd(&rs->cur.attempted, (unsigned long long)att);
         if (sk) atomicAdd(&rs->cur.skipped, (unsigned long long)sk);
+        unsigned long long pe = 0, pb = 0;
+        for (int w = 0; w < kWarps; ++w) { pe += s_pk[w][0]; pb += s_pk[w][1]; }
+        if (pe) {
+            atomicAdd(&rs->cur.packed_edges, pe);
+            atomicAdd(&rs->cur.code_bytes, pb);
+        }
     }
     __syncthreads();
 #pragma unroll

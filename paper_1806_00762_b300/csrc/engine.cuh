@@ -39,6 +39,8 @@ struct WindowDesc {
 // Counters of one sweep, copied to the host at the sweep boundary.
 struct SweepReport {
     unsigned long long changed, attempted, skipped, edges;
+    unsigned long long packed_edges, code_bytes;  // in-edges and LEB128 bytes of attempted
+                                                  // vertices on packed pages
     unsigned int overflow, thr_min, passes_run, passes_skipped;
     double resid, dangling;
 };
@@ -96,6 +98,9 @@ struct AlgoArgs {
     uint32_t bfs_lb;          // BFS: no attempted vertex can reach a level below this, so a
                               // lane that finds it stops scanning (early-break pull)
     float omega;              // PageRank over-relaxation factor of the apply step (1 = plain)
+    uint32_t* chg_stamp;      // push stage on: tag of the sweep in which a vertex last
+                              // changed (written with every value change), else null
+    uint32_t chg_tag;         // tag of the current sweep
 };
 
 // Launchers (engine.cu).  `pass` is the global pass counter (its parity picks

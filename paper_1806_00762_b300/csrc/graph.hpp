@@ -17,9 +17,11 @@ struct RunWorkspace {
     seraph::DevBuf<uint32_t> val, out;           // values; caller-order output staging
     seraph::DevBuf<float> x, contrib, x_next, x_prev, inv_out;
     seraph::DevBuf<uint8_t> state;
+    seraph::DevBuf<uint32_t> stamp, front0, front1, big;  // push stage
     void release() {
         ebuf.release(); lists.release(); val.release(); out.release(); x.release();
         contrib.release(); x_next.release(); x_prev.release(); inv_out.release(); state.release();
+        stamp.release(); front0.release(); front1.release(); big.release();
     }
 };
 
@@ -71,6 +73,12 @@ struct seraph_graph {
     bool reordered = false;            // built with SERAPH_REORDER
     seraph::DevBuf<uint32_t> d_perm;   // internal id -> caller's id (reordered only)
     seraph::DevBuf<uint32_t> d_inv;    // caller's id -> internal id (reordered only)
+    // Out-edge CSR of the kept edges in internal ids (SERAPH_OUT_EDGES), in
+    // pinned memory that kernels read directly over the host link (the push
+    // stage of sparse sweeps): u64 offsets (n+1), u32 destinations ascending
+    // per source, weights in the stored width.
+    bool out_edges = false;
+    seraph::PinnedBuf h_out_off, h_out_col, h_out_w;
 };
 
 namespace seraph {
@@ -98,6 +106,9 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src,
 void build_graph_csr(seraph_graph* g, uint64_t n, const uint64_t* row_off, const uint32_t* col,
                      const uint32_t* w, int mem, uint32_t flags, uint32_t num_pages,
                      cudaStream_t s);
+// CSR offsets in host memory: n in range, row_off[0] == 0, non-decreasing
+// (SERAPH_EINVAL otherwise).  Touches no device.
+void check_csr_offsets_host(uint64_t n, const uint64_t* row_off);
 void export_csc(const seraph_graph* g, uint64_t* col_off, uint32_t* row, uint32_t* w,
                 uint32_t* out_degree);
 }  // namespace seraph

@@ -416,6 +416,15 @@ __global__ void stage_off_kernel(const uint64_t* __restrict__ col_off,
     }
 }
 
+// Flags CSR offsets that do not start at 0 or decrease somewhere.
+__global__ void check_csr_kernel(const uint64_t* __restrict__ row_off, uint64_t n,
+                                 unsigned* __restrict__ bad) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        if ((v == 0 && row_off[0] != 0) || row_off[v] > row_off[v + 1]) atomicOr(bad, 1u);
+    }
+}
+
 __global__ void expand_csr_kernel(const uint64_t* __restrict__ row_off, uint64_t n,
                                   uint32_t* __restrict__ src) {
     uint64_t E = row_off[n];
@@ -456,6 +465,24 @@ __global__ void relabel_keys_kernel(const uint32_t* __restrict__ col, const uint
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E;
          e += (uint64_t)gridDim.x * blockDim.x)
         keys[e] = ((uint64_t)inv[dcol[e]] << b) | inv[col[e]];
+}
+
+// Out-edge keys (source << b) | destination of the CSC's edges (dst[e] is
+// edge e's destination), with the stored weight widened to 32 bits.
+__global__ void out_keys_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                                const uint8_t* __restrict__ w, int wb, uint64_t E, int b,
+                                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        keys[e] = ((uint64_t)src[e] << b) | dst[e];
+        if (vals) {
+            uint32_t x = 0;
+            if (wb == 1) x = w[e];
+            else if (wb == 2) x = ((const uint16_t*)w)[e];
+            else x = ((const uint32_t*)w)[e];
+            vals[e] = x;
+        }
+    }
 }
 
 __global__ void split_keys_kernel(const uint64_t* __restrict__ keys, uint64_t E, int b,
@@ -694,6 +721,62 @@ void sorted_adjacency(uint64_t n, uint64_t m, const uint32_t* lo_in, const uint3
     SR_CUDA(cudaStreamSynchronize(s));
 }
 
+// Out-edge CSR (SERAPH_OUT_EDGES) from the CSC: every kept edge as the key
+// (source << b) | destination with its weight, sorted, then split into
+// offsets per source and destinations ascending; copied into pinned memory.
+void build_out_edges(seraph_graph* g, uint64_t n, uint64_t E, DevBuf<uint32_t>& col,
+                     const DevBuf<uint64_t>& col_off, const uint8_t* wsrc, bool weighted,
+                     cudaStream_t s) {
+    const int b = bits_for(n);
+    g->h_out_off.alloc(8 * (n + 1), true);
+    if (E) g->h_out_col.alloc(4 * E, true);
+    if (weighted && E) g->h_out_w.alloc((uint64_t)g->wbytes * E, true);
+    DevBuf<uint64_t> out_off(n + 1);
+    if (E) {
+        DevBuf<uint64_t> keys(E), keys_alt(E);
+        DevBuf<uint32_t> vals, vals_alt;
+        {
+            DevBuf<uint32_t> dst(E);
+            expand_csr_kernel<<<grid_for(E), kNT, 0, s>>>(col_off.p, n, dst.p);
+            SR_LAUNCH();
+            if (weighted) { vals.alloc(E); vals_alt.alloc(E); }
+            out_keys_kernel<<<grid_for(E), kNT, 0, s>>>(col.p, dst.p, wsrc, (int)g->wbytes, E, b,
+                                                       keys.p, vals.p);
+            SR_LAUNCH();
+            SR_CUDA(cudaStreamSynchronize(s));
+        }
+        radix_sort(keys, keys_alt, vals, vals_alt, E, 2 * b, s);
+        keys_alt.release();
+        vals_alt.release();
+        DevBuf<uint32_t> ocol(E), osrc(E);
+        split_keys_kernel<<<grid_for(E), kNT, 0, s>>>(keys.p, E, b, ocol.p, osrc.p);
+        SR_LAUNCH();
+        col_off_kernel<<<grid_for(n + 1), kNT, 0, s>>>(osrc.p, E, n, out_off.p);
+        SR_LAUNCH();
+        SR_CUDA(cudaStreamSynchronize(s));
+        keys.release();
+        osrc.release();
+        SR_CUDA(cudaMemcpyAsync(g->h_out_col.p, ocol.p, 4 * E, cudaMemcpyDeviceToHost, s));
+        if (weighted) {
+            if (g->wbytes < 4) {
+                DevBuf<uint8_t> wn((uint64_t)g->wbytes * E);
+                narrow_kernel<<<grid_for(E), kNT, 0, s>>>(vals.p, E, (int)g->wbytes, wn.p);
+                SR_LAUNCH();
+                SR_CUDA(cudaMemcpyAsync(g->h_out_w.p, wn.p, (uint64_t)g->wbytes * E,
+                                        cudaMemcpyDeviceToHost, s));
+                SR_CUDA(cudaStreamSynchronize(s));
+            } else {
+                SR_CUDA(cudaMemcpyAsync(g->h_out_w.p, vals.p, 4 * E, cudaMemcpyDeviceToHost, s));
+            }
+        }
+    } else {
+        SR_CUDA(cudaMemsetAsync(out_off.p, 0, 8 * (n + 1), s));
+    }
+    SR_CUDA(cudaMemcpyAsync(g->h_out_off.p, out_off.p, 8 * (n + 1), cudaMemcpyDeviceToHost, s));
+    SR_CUDA(cudaStreamSynchronize(s));
+    g->out_edges = true;
+}
+
 // The packed page form (SERAPH_COMPRESS): LEB128 gap streams of every
 // destination's sources, encoded on the device, then laid out per page in
 // pinned memory as off (copied from `stage`), boff and the stream bytes.
@@ -778,7 +861,8 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     SR_CHECK(mem == SERAPH_MEM_HOST || mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad mem kind");
     SR_CHECK(m == 0 || (src_in && dst_in), SERAPH_EINVAL, "src/dst must not be NULL");
     SR_CHECK(m < (1ull << 36), SERAPH_EINVAL, "too many edges");
-    SR_CHECK((flags & ~(SERAPH_SYMMETRIZE | SERAPH_REORDER | SERAPH_COMPRESS)) == 0, SERAPH_EINVAL,
+    SR_CHECK((flags & ~(SERAPH_SYMMETRIZE | SERAPH_REORDER | SERAPH_COMPRESS | SERAPH_OUT_EDGES)) == 0,
+             SERAPH_EINVAL,
              "unknown flag");
     const bool sym = flags & SERAPH_SYMMETRIZE;
     const bool reorder = flags & SERAPH_REORDER;
@@ -893,17 +977,40 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     }
     SR_CUDA(cudaStreamSynchronize(s));
     if (flags & SERAPH_COMPRESS) build_packed(g, n, E, col.p, col_off.p, d_vb.p, d_st.p, st, stage, s);
+    if (flags & SERAPH_OUT_EDGES) {
+        stage.release();
+        build_out_edges(g, n, E, col, col_off, wsrc, weighted, s);
+    }
+}
+
+void check_csr_offsets_host(uint64_t n, const uint64_t* row_off) {
+    SR_CHECK(n >= 1 && n <= 0xFFFFFFFEull, SERAPH_EINVAL, "n must be in [1, 2^32-2]");
+    SR_CHECK(row_off != nullptr, SERAPH_EINVAL, "row_off must not be NULL");
+    SR_CHECK(row_off[0] == 0, SERAPH_EINVAL, "row_off[0] must be 0");
+    for (uint64_t v = 0; v < n; ++v)
+        SR_CHECK(row_off[v] <= row_off[v + 1], SERAPH_EINVAL,
+                 "row_off must be non-decreasing (row_off[" + std::to_string(v) + "] > row_off[" +
+                     std::to_string(v + 1) + "])");
 }
 
 void build_graph_csr(seraph_graph* g, uint64_t n, const uint64_t* row_off_in, const uint32_t* col_in,
                      const uint32_t* w_in, int mem, uint32_t flags, uint32_t P, cudaStream_t s) {
     SR_CHECK(n >= 1 && n <= 0xFFFFFFFEull, SERAPH_EINVAL, "n must be in [1, 2^32-2]");
     SR_CHECK(row_off_in != nullptr, SERAPH_EINVAL, "row_off must not be NULL");
+    SR_CHECK(mem == SERAPH_MEM_HOST || mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad mem kind");
     uint64_t m = 0;
     if (mem == SERAPH_MEM_DEVICE) {
+        DevBuf<unsigned> bad(1);
+        SR_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+        check_csr_kernel<<<grid_for(n), kNT, 0, s>>>(row_off_in, n, bad.p);
+        SR_LAUNCH();
+        unsigned nbad = 0;
+        SR_CUDA(cudaMemcpyAsync(&nbad, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         SR_CUDA(cudaMemcpyAsync(&m, row_off_in + n, 8, cudaMemcpyDeviceToHost, s));
         SR_CUDA(cudaStreamSynchronize(s));
+        SR_CHECK(nbad == 0, SERAPH_EINVAL, "row_off must start at 0 and be non-decreasing");
     } else {
+        check_csr_offsets_host(n, row_off_in);
         m = row_off_in[n];
     }
     DevBuf<uint64_t> hro;

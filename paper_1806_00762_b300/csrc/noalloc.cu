@@ -29,7 +29,8 @@ namespace {
 
 using seraph::kFull;
 
-constexpr uint32_t kCounters = 64;  // [0] changes in the pass, [1] list length, [2] overflow
+constexpr uint32_t kCounters = 64;  // [0] changes in the pass, [1] list length, [2] overflow,
+                                    // [3] input check: 1 bad offsets, 2 a source id >= n
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) uint32_t g_noalloc_scratch[kCounters + SERAPH_NOALLOC_MAX_VERTICES];
@@ -50,6 +51,23 @@ uint32_t* scratch_on_current_device() {
         g_scratch_addr[dev] = (uint32_t*)p;
     }
     return g_scratch_addr[dev];
+}
+
+// Input check before anything is read through the CSC: offsets that do not
+// start at 0 or that decrease, and source ids >= n (which would index
+// outside `values`), are flagged in scratch[3].
+__global__ void na_check(const uint64_t* __restrict__ col_off, const uint32_t* __restrict__ row,
+                         uint32_t n, uint32_t* scratch) {
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    unsigned bad = 0;
+    for (uint64_t v = tid; v < n; v += stride)
+        if ((v == 0 && col_off[0] != 0) || col_off[v] > col_off[v + 1]) bad |= 1u;
+    const uint64_t m = col_off[n];
+    for (uint64_t k = tid; k < m; k += stride)
+        if (row[k] >= n) bad |= 2u;
+    bad = __reduce_or_sync(kFull, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicOr(&scratch[3], bad);
 }
 
 __global__ void na_init(int algo, uint32_t n, uint32_t source, uint32_t* values) {
@@ -117,12 +135,20 @@ int run_noalloc(int algo, uint64_t n, const uint64_t* col_off, const uint32_t* r
     SR_CHECK(n <= SERAPH_NOALLOC_MAX_VERTICES, SERAPH_EINVAL,
              "n exceeds SERAPH_NOALLOC_MAX_VERTICES (2^20) of the static scratch");
     SR_CHECK(col_off && values, SERAPH_EINVAL, "col_off and values must not be NULL");
+    SR_CHECK(row != nullptr, SERAPH_EINVAL, "row must not be NULL");
     if (algo != SERAPH_CC) SR_CHECK(source < n, SERAPH_EINVAL, "source >= n");
     uint32_t* scratch = scratch_on_current_device();
     const uint32_t nn = (uint32_t)n;
     const int sms = seraph::device_sms();
     const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
     SR_CUDA(cudaMemsetAsync(scratch, 0, kCounters * sizeof(uint32_t), s));
+    na_check<<<(unsigned)sms * 8, 256, 0, s>>>(col_off, row, nn, scratch);
+    SR_LAUNCH();
+    uint32_t check = 0;
+    SR_CUDA(cudaMemcpyAsync(&check, scratch + 3, sizeof(check), cudaMemcpyDeviceToHost, s));
+    SR_CUDA(cudaStreamSynchronize(s));
+    SR_CHECK(!(check & 1u), SERAPH_EINVAL, "col_off must start at 0 and be non-decreasing");
+    SR_CHECK(!(check & 2u), SERAPH_EINVAL, "a source id in row is >= n");
     na_init<<<grid, 256, 0, s>>>(algo, nn, source, values);
     na_list<<<grid, 256, 0, s>>>(col_off, nn, scratch);
     SR_LAUNCH();

@@ -32,6 +32,7 @@
 #include "engine.cuh"
 #include "graph.hpp"
 #include "mlp.cuh"
+#include "push.cuh"
 
 namespace seraph {
 namespace {
@@ -200,6 +201,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CHECK(!(learned || trace) || P->window == 1, SERAPH_EINVAL,
              "learned schedules and traces need window = 1");
     const SchedModel* model = learned ? &((seraph_sched_model*)P->sched_model)->model : nullptr;
+    SR_CHECK(P->push <= 1, SERAPH_EINVAL, "push must be 0 or 1");
+    SR_CHECK(!P->push || P->algo != SERAPH_PAGERANK, SERAPH_EINVAL,
+             "the push stage is for SSSP, BFS and CC");
+    SR_CHECK(!P->push || g->out_edges, SERAPH_EINVAL,
+             "the push stage needs a graph built with SERAPH_OUT_EDGES");
+    SR_CHECK(!P->push || !learned, SERAPH_EINVAL, "the push stage needs a fixed schedule");
+    SR_CHECK(!P->push || !(P->algo == SERAPH_CC && !g->symmetrized), SERAPH_EINVAL,
+             "CC with the push stage needs a symmetrized graph");
     const uint64_t n = g->n;
     int algo = P->algo;
     if ((algo == SERAPH_SSSP || algo == SERAPH_BFS))
@@ -306,26 +315,32 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     DevBuf<uint32_t> val, caller_order;
     DevBuf<float> x, contrib, x_next, x_prev, inv_out;
     DevBuf<uint8_t> state;
+    DevBuf<uint32_t> stamp, front0, front1, big;
     // borrow the graph's kept buffers for this run (given back on every exit)
     struct Lease {
         RunWorkspace* ws = nullptr;
         DevBuf<uint8_t>* ebuf; DevBuf<unsigned long long>* lists; DevBuf<uint32_t>* val;
-        DevBuf<uint32_t>* out; DevBuf<float>* f[5]; DevBuf<uint8_t>* state;
+        DevBuf<uint32_t>* out; DevBuf<float>* f[5]; DevBuf<uint8_t>* state; DevBuf<uint32_t>* pu[4];
         ~Lease() {
             if (!ws) return;
             ws->ebuf = std::move(*ebuf); ws->lists = std::move(*lists); ws->val = std::move(*val);
             ws->out = std::move(*out); ws->x = std::move(*f[0]); ws->contrib = std::move(*f[1]);
             ws->x_next = std::move(*f[2]); ws->x_prev = std::move(*f[3]);
             ws->inv_out = std::move(*f[4]); ws->state = std::move(*state);
+            ws->stamp = std::move(*pu[0]); ws->front0 = std::move(*pu[1]);
+            ws->front1 = std::move(*pu[2]); ws->big = std::move(*pu[3]);
             ws->m.unlock();
         }
-    } lease{nullptr, &ebuf, &lists, &val, &caller_order, {&x, &contrib, &x_next, &x_prev, &inv_out}, &state};
+    } lease{nullptr, &ebuf, &lists, &val, &caller_order, {&x, &contrib, &x_next, &x_prev, &inv_out}, &state,
+            {&stamp, &front0, &front1, &big}};
     if (g->ws.m.try_lock()) {
         RunWorkspace& w = g->ws;
         ebuf = std::move(w.ebuf); lists = std::move(w.lists); val = std::move(w.val);
         caller_order = std::move(w.out); x = std::move(w.x); contrib = std::move(w.contrib);
         x_next = std::move(w.x_next); x_prev = std::move(w.x_prev); inv_out = std::move(w.inv_out);
         state = std::move(w.state);
+        stamp = std::move(w.stamp); front0 = std::move(w.front0); front1 = std::move(w.front1);
+        big = std::move(w.big);
         lease.ws = &w;
     }
     auto ensure = [](auto& buf, size_t count) { if (buf.n < count) buf.alloc(count); };
@@ -352,6 +367,17 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         ensure(val, n);
     }
     if (P->pvu == SERAPH_PVU_WEAK) ensure(state, n);
+    const bool push_on = P->push != 0;
+    const uint64_t big_cap = std::min<uint64_t>(n, g->m / kPushWarpMax + 1);
+    DevBuf<PushState> d_ps;
+    PinnedBuf h_ps;
+    if (push_on) {
+        ensure(stamp, n); ensure(front0, n); ensure(front1, n); ensure(big, big_cap);
+        SR_CUDA(cudaMemsetAsync(stamp.p, 0, n * sizeof(uint32_t), cs.s));
+        d_ps.alloc(1);
+        h_ps.alloc(sizeof(PushState));
+    }
+    const uint64_t push_below = P->push_below ? P->push_below : std::max<uint64_t>(n / 256, 1);
 
     AlgoArgs a{};
     a.val = is_pr ? nullptr : val.p;  // (borrowed buffers of other algorithms stay unused)
@@ -384,6 +410,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     a.wbytes = (uint8_t)g->wbytes;
     a.packed = packed;
     a.n = (uint32_t)n;
+    a.chg_stamp = push_on ? stamp.p : nullptr;
+    a.chg_tag = 1;
     {
         uint64_t hot_bytes = P->l2_hot_bytes;
         if (hot_bytes == SERAPH_L2_HOT_AUTO) {
@@ -603,6 +631,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     bool pr_predict_off = false;
     int rc = SERAPH_OK;
     std::vector<int64_t> proc_step(C, -1);  // last prediction-off step that processed a chunk
+    // tag of the last sweep in which a chunk was processed with every vertex
+    // relaxed or final (prediction off, or strong conditions); 0 = none yet
+    std::vector<uint32_t> valid_tag(C, 0);
     int64_t last_change = -1;               // last step with a value change (init = step -1)
     uint64_t sweep_first_step = 0;
     std::vector<uint8_t> pred_in_step(ring, 0);
@@ -614,6 +645,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     std::vector<uint32_t> seq_of(C, 0);  // load sequence number of each chunk
     for (uint64_t t = 0;; ++t) {
         const std::vector<uint32_t>& win = sched.window(t);
+        a.chg_tag = S.sweeps + 1;  // value changes of this sweep carry its tag
         // (0) anything step t needs that could not be prefetched
         for (uint32_t c : win)
             if (slot_of[c] < 0) {
@@ -742,6 +774,10 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             if (steps_changed[s % ring]) last_change = (int64_t)s;
             if (!pred_in_step[s % ring] || !P->verify)
                 for (uint32_t c : window_of[s % ring]) proc_step[c] = (int64_t)s;
+            // every vertex of the chunk relaxed or final (for the push stage);
+            // strong skips count as final where every sweep visits every chunk
+            if (!pred_in_step[s % ring] || (P->pvu == SERAPH_PVU_STRONG && !zig))
+                for (uint32_t c : window_of[s % ring]) valid_tag[c] = S.sweeps + 1;
         }
         // clear the ring entries of this sweep for reuse
         SR_CUDA(cudaMemsetAsync(d_steps.p, 0, ring * sizeof(unsigned), cs.s));
@@ -749,6 +785,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         S.passes_run += rep.passes_run;
         S.passes_skipped += rep.passes_skipped;
         S.edges_relaxed += rep.edges;
+        S.packed_edges += rep.packed_edges;
+        S.code_bytes += rep.code_bytes;
         S.vertices_attempted += rep.attempted;
         S.vertices_skipped += rep.skipped;
         S.changes += rep.changed;
@@ -800,6 +838,58 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
                 predict = false;  // a predicted sweep changed nothing: retrieve with all-pull
             } else {
                 predict = P->pvu != SERAPH_PVU_OFF;
+            }
+            // dense -> sparse switch.  Every chunk was last processed with all of
+            // its vertices relaxed or final in sweep valid_tag[c] or later, so an
+            // edge can be violated only if its source changed since the earliest
+            // of those sweeps (tag_first): those vertices start the push stage.
+            // (Zigzag orders skip a sweep's boundary chunk in the next sweep, so
+            // tag_first may lie one sweep back.)
+            const uint32_t tag_first = *std::min_element(valid_tag.begin(), valid_tag.end());
+            if (!stop && push_on && !S.push_sweep && rep.changed > 0 && rep.changed <= push_below &&
+                tag_first > 0) {
+                S.push_sweep = S.sweeps;
+                PushArgs pa{};
+                pa.out_off = g->h_out_off.device_ptr<uint64_t>();
+                pa.out_col = g->h_out_col.device_ptr<uint32_t>();
+                pa.out_w = use_w ? g->h_out_w.device_ptr<uint8_t>() : nullptr;
+                pa.wbytes = g->wbytes;
+                pa.n = (uint32_t)n;
+                pa.val = val.p;
+                pa.stamp = stamp.p;
+                pa.front[0] = front0.p;
+                pa.front[1] = front1.p;
+                pa.big = big.p;
+                pa.big_cap = (uint32_t)big_cap;
+                pa.ps = d_ps.p;
+                const uint32_t tag_last = S.sweeps;  // the tag of the sweep that just closed
+                launch_push_frontier(pa, tag_first, cs.s);
+                launches += 1;
+                PushState hps{};
+                const int ialgo = algo == SERAPH_SSSP ? ALG_SSSP : algo == SERAPH_BFS ? ALG_BFS : ALG_CC;
+                for (uint32_t r = 0;;) {
+                    // rounds in batches of 8 (a round after the frontier ran dry does nothing)
+                    for (int k = 0; k < 8; ++k, ++r) launch_push_round(ialgo, pa, r, tag_last + 1 + r, cs.s);
+                    launches += 8 * 3;
+                    SR_CUDA(cudaMemcpyAsync(h_ps.p, d_ps.p, sizeof(PushState), cudaMemcpyDeviceToHost, cs.s));
+                    SR_CUDA(cudaEventRecord(ev_sweep.e, cs.s));
+                    wait_event(ev_sweep.e, P->timeout_ms);
+                    std::memcpy(&hps, h_ps.p, sizeof(hps));
+                    if (hps.cnt[r & 1] == 0) break;
+                    SR_CHECK(r < n + 16, SERAPH_ENOTCONV, "push stage: no fixpoint after n rounds");
+                }
+                S.push_rounds = hps.rounds;
+                S.push_edges = hps.edges;
+                S.changes += hps.changes;
+                if (!hps.ovf) {
+                    S.converged = 1;
+                    stop = true;
+                } else {
+                    // a candidate overflowed: a prediction-off pull sweep over every
+                    // chunk decides SERAPH_EOVERFLOW as without the push stage
+                    predict = false;
+                    last_change = (int64_t)t;
+                }
             }
             if (!stop && S.sweeps >= P->max_sweeps) { rc = SERAPH_ENOTCONV; stop = true; }
         }

@@ -28,6 +28,10 @@ def test_algo_bytes_counts():
     assert bench.algo_bytes("sssp", st, 4, weak=True) == 12 * 100 + 16 * 10 + 4 * 3 + 2 * 10
     # PageRank: 8 B per edge + 20 B per vertex
     assert bench.algo_bytes("pagerank", st) == 8 * 100 + 20 * 10
+    # packed pages: their edges' column bytes are the code bytes, not 4 B each
+    pk = dict(st, packed_edges=60, code_bytes=90)
+    assert bench.algo_bytes("pagerank", pk) == 4 * 40 + 90 + 4 * 100 + 20 * 10
+    assert bench.algo_bytes("sssp", pk, 1) == 4 * 40 + 90 + 5 * 100 + 16 * 10 + 4 * 3
 
 
 def test_pipeline_roofline_takes_the_slower_side():

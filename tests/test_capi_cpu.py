@@ -125,3 +125,31 @@ def test_gather_probe_rejects_bad_arguments_before_any_device_call():
         assert rc == C.SERAPH_EINVAL, (nv, ng, hot, frac, reps)
         assert lib.seraph_last_error()
     assert lib.seraph_gather_probe(16, 8, 4, 0.5, 1, None, None) == C.SERAPH_EINVAL
+
+
+def test_from_csr_rejects_bad_host_offsets_before_any_device_call():
+    """Host CSR offsets that do not start at 0 or that decrease are rejected
+    with SERAPH_EINVAL before the library touches a device (so without a GPU
+    too), each with a message naming the problem."""
+    import numpy as np
+    col = np.array([1, 2, 0], dtype=np.uint32)
+    cases = [
+        (np.array([1, 2, 3, 3], dtype=np.uint64), b"row_off[0]"),       # does not start at 0
+        (np.array([0, 2, 1, 3], dtype=np.uint64), b"non-decreasing"),   # decreases at v = 1
+        (np.array([0, 1, 2, 1], dtype=np.uint64), b"non-decreasing"),   # decreases at the end
+    ]
+    for ro, what in cases:
+        with pytest.raises(C.SeraphError) as ei:
+            seraph.Graph.from_csr(3, ro, col)
+        assert ei.value.code == C.SERAPH_EINVAL
+        assert what in C.lib().seraph_last_error()
+    with pytest.raises(C.SeraphError) as ei:
+        seraph.Graph.from_csr(0, np.zeros(1, dtype=np.uint64), col)
+    assert ei.value.code == C.SERAPH_EINVAL
+
+
+def test_pinned_fault_injection_hook_arms_and_disarms_without_gpu():
+    assert seraph.debug_pinned_bytes() == 0
+    seraph.debug_fail_pinned_alloc(3)
+    seraph.debug_fail_pinned_alloc(0)
+    assert seraph.debug_pinned_bytes() == 0
