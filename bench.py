@@ -41,7 +41,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-fixpoint and effective GTEPS, RMAT-28 streamed; learned vs fixed sched"
 
 
-DEFAULT_SSSP = "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid"
+DEFAULT_SSSP = "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid,push=1"
 DEFAULT_PAGERANK = "order=zigzag,window=1,slots=14,pvu=weak,columns=hybrid,pr_normalize=1,pr_omega=1.15"
 
 
@@ -153,7 +153,7 @@ def link_gbps(torch, nbytes=1 << 30, reps=5, chunks=4) -> float:
     return chunks * nbytes / (best / 1e3) / 1e9
 
 
-def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True):
+def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True, out_edges=True):
     n = 1 << scale
     m = synth.rmat_config(scale).m
     src = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -161,7 +161,8 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True)
     w = torch.empty_like(src)
     synth.rmat_edges_device(scale, src.data_ptr(), dst.data_ptr(), w.data_ptr())
     torch.cuda.synchronize()
-    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=pages, reorder=reorder, compress=compress)
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=pages, reorder=reorder, compress=compress,
+                                out_edges=out_edges)
     del src, dst, w
     torch.cuda.empty_cache()
     return g
@@ -171,7 +172,7 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True)
 # capture of the default step (profiles/launches_rmat28_sssp_pagerank.md);
 # valid only for the kernel source and the two schedules it was taken on.
 RELAX_TRAFFIC = {"engine_sha256": "12bf6fac3d30c341", "bytes_per_launch": 5.220801756e9,
-                 "sssp": "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid",
+                 "sssp": "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid,push=1",
                  "pagerank": "order=zigzag,window=1,slots=14,pvu=weak,columns=hybrid,"
                              "pr_normalize=1,pr_omega=1.15",
                  "workload": "rmat28 default step"}
@@ -605,7 +606,11 @@ def main():
         ladder = [(nm, ks, dict(kp, pr_normalize=0, pr_omega=1.0)) for nm, ks, kp in ladder]
         ladder.append(("resident+pvu+hybrid+pr_unit_sum", sched["sssp"],
                        dict(sched["pagerank"], pr_normalize=1, pr_omega=1.0)))
-        ladder.append(("resident+pvu+hybrid+pr_unit_sum+sor", sched["sssp"],
+        nopush = {k: v for k, v in sched["sssp"].items() if k != "push"}
+        ladder = [(nm, {k: v for k, v in ks.items() if k != "push"}, kp) for nm, ks, kp in ladder]
+        ladder.append(("resident+pvu+hybrid+pr_unit_sum+sor", nopush,
+                       dict(sched["pagerank"], pr_normalize=1)))
+        ladder.append(("resident+pvu+hybrid+pr_unit_sum+sor+push", dict(nopush, push=1),
                        dict(sched["pagerank"], pr_normalize=1)))
         line["ablation"] = {}
         for name, ks, kp in ladder:

@@ -300,11 +300,19 @@ typedef struct seraph_params {
                                    the graph's out-edge CSR (SERAPH_OUT_EDGES),
                                    round by round on the GPU, until a round
                                    changes nothing: the fixpoint.  SSSP, BFS
-                                   and CC (on a symmetrized graph); fixed
-                                   schedules only.  0 = off                  */
+                                   and CC (on a symmetrized graph).  0 = off */
     uint32_t pad2;
     uint64_t push_below;        /* switch threshold in changed vertices (0 =
                                    n / 256)                                  */
+    uint32_t count_clean;       /* measurement (SSSP, BFS, CC): 1 = at every
+                                   sweep close count the pages none of whose
+                                   in-edge sources changed in that sweep (the
+                                   pages active-page skipping could leave out
+                                   of the next sweep), into stats.clean_pages;
+                                   sources are grouped in 1024 blocks of
+                                   consecutive ids, so the count is a lower
+                                   bound                                     */
+    uint32_t pad3;
 } seraph_params;
 
 #define SERAPH_L2_HOT_AUTO UINT64_MAX
@@ -344,6 +352,9 @@ typedef struct seraph_stats {
     uint64_t push_edges;        /* out-edges read by the push stage           */
     uint32_t push_rounds;       /* push rounds with a non-empty frontier      */
     uint32_t push_sweep;        /* sweeps run before the switch (0: none)     */
+    uint64_t clean_pages;       /* count_clean: pages, summed over sweeps,
+                                   with no in-edge source block changed in
+                                   the sweep                                 */
 } seraph_stats;
 
 int seraph_params_default(seraph_params* p, int algo);

@@ -67,7 +67,7 @@ class Params(ctypes.Structure):
                 ("group8_max_deg", u32),
                 ("sched_model", vp), ("stream", vp), ("trace", vp), ("columns", u32),
                 ("pad1", u32), ("l2_hot_bytes", u64), ("pr_omega", dbl), ("push", u32),
-                ("pad2", u32), ("push_below", u64)]
+                ("pad2", u32), ("push_below", u64), ("count_clean", u32), ("pad3", u32)]
 
 
 class Stats(ctypes.Structure):
@@ -78,7 +78,7 @@ class Stats(ctypes.Structure):
                 ("copy_ms", dbl), ("compute_ms", dbl), ("wall_ms", dbl), ("residual", dbl),
                 ("relax_ms", dbl), ("relax_launches", u64), ("kernel_launches", u64),
                 ("packed_edges", u64), ("code_bytes", u64), ("push_edges", u64),
-                ("push_rounds", u32), ("push_sweep", u32)]
+                ("push_rounds", u32), ("push_sweep", u32), ("clean_pages", u64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1123,6 +1123,37 @@ __global__ void __launch_bounds__(kNT) pr_close_final_kernel(RunState* rs, const
     }
 }
 
+__global__ void __launch_bounds__(kNT) dirty_blocks_kernel(const uint32_t* __restrict__ stamp,
+                                                           uint64_t n, uint32_t tag, uint32_t bsz,
+                                                           uint32_t* __restrict__ dirty) {
+    __shared__ uint32_t bits[32];
+    if (threadIdx.x < 32) bits[threadIdx.x] = 0;
+    __syncthreads();
+    // bsz is a multiple of 32, so the 32 vertices of a warp share one block
+    for (uint64_t v0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull; v0 < n;
+         v0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = v0 + lane_id();
+        if (__any_sync(kFull, v < n && stamp[v] == tag) && lane_id() == 0) {
+            const uint32_t blk = (uint32_t)(v0 / bsz);
+            atomicOr(&bits[blk >> 5], 1u << (blk & 31));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && bits[threadIdx.x]) atomicOr(&dirty[threadIdx.x], bits[threadIdx.x]);
+}
+
+__global__ void clean_pages_kernel(const uint32_t* __restrict__ page_blocks, uint32_t P,
+                                   const uint32_t* __restrict__ dirty, RunState* rs) {
+    unsigned clean = 0;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        uint32_t hit = 0;
+        for (int w = 0; w < 32; ++w) hit |= page_blocks[(uint64_t)p * 32 + w] & dirty[w];
+        clean += hit == 0;
+    }
+    clean = __reduce_add_sync(kFull, clean);
+    if (lane_id() == 0 && clean) atomicAdd(&rs->cur.clean_pages, (unsigned long long)clean);
+}
+
 unsigned grid_1d(uint64_t n) {
     uint64_t b = (n + kNT - 1) / kNT, cap = (uint64_t)device_sms() * 16;
     return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
@@ -1218,6 +1249,15 @@ void launch_init_pr(const uint32_t* outdeg, const AlgoArgs& a, float* x_prev, ui
                     cudaStream_t s) {
     init_pr_kernel<<<grid_1d(n), kNT, 0, s>>>(outdeg, a.x, a.contrib, x_prev,
                                                const_cast<float*>(a.inv_out), a.state, n);
+    SR_LAUNCH();
+}
+
+void launch_count_clean(const uint32_t* stamp, uint64_t n, uint32_t tag, uint32_t bsz,
+                        const uint32_t* page_blocks, uint32_t P, uint32_t* dirty, RunState* rs,
+                        cudaStream_t s) {
+    SR_CUDA(cudaMemsetAsync(dirty, 0, 32 * sizeof(uint32_t), s));
+    dirty_blocks_kernel<<<grid_1d(n), kNT, 0, s>>>(stamp, n, tag, bsz, dirty);
+    clean_pages_kernel<<<(P + kNT - 1) / kNT, kNT, 0, s>>>(page_blocks, P, dirty, rs);
     SR_LAUNCH();
 }
 

@@ -41,6 +41,7 @@ struct SweepReport {
     unsigned long long changed, attempted, skipped, edges;
     unsigned long long packed_edges, code_bytes;  // in-edges and LEB128 bytes of attempted
                                                   // vertices on packed pages
+    unsigned long long clean_pages;  // pages with no in-edge source changed in the sweep
     unsigned int overflow, thr_min, passes_run, passes_skipped;
     double resid, dangling;
 };
@@ -132,6 +133,13 @@ void launch_unpermute(const uint32_t* in, const uint32_t* inv, uint64_t n, uint3
 void launch_init_pr(const uint32_t* outdeg, const AlgoArgs& a, float* x_prev, uint64_t n,
                     cudaStream_t s);
 void launch_close_min(RunState* rs, SweepReport* out, cudaStream_t s);
+// Active-page measurement at a sweep close: the source blocks holding a vertex
+// whose stamp is `tag` (changed in the closing sweep; `dirty` = 32 words of
+// scratch), then rs->cur.clean_pages += the pages whose source-block bitmap
+// (32 words per page) misses all of them.
+void launch_count_clean(const uint32_t* stamp, uint64_t n, uint32_t tag, uint32_t bsz,
+                        const uint32_t* page_blocks, uint32_t P, uint32_t* dirty, RunState* rs,
+                        cudaStream_t s);
 void launch_close_pr(const AlgoArgs& a, uint64_t n, float* x_prev, double damping,
                      double* partial, int nparts, SweepReport* out, bool normalize,
                      cudaStream_t s);

@@ -79,7 +79,17 @@ struct seraph_graph {
     // per source, weights in the stored width.
     bool out_edges = false;
     seraph::PinnedBuf h_out_off, h_out_col, h_out_w;
+    // Which source blocks each page reads: bit b of page p's kPageBlockWords
+    // words is set when some in-edge of p comes from a vertex of block b
+    // (blocks of src_block consecutive internal ids).  Measures how many
+    // pages a change leaves untouched (active-page skipping).
+    seraph::DevBuf<uint32_t> d_page_blocks;
+    uint32_t src_block = 0;
 };
+
+namespace seraph {
+constexpr uint32_t kPageBlockWords = 32;  // 1024 source blocks
+}
 
 namespace seraph {
 struct Adjacency;

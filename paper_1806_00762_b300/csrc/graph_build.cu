@@ -361,6 +361,23 @@ __global__ void zero_in_kernel(const uint64_t* __restrict__ col_off, uint64_t n,
     }
 }
 
+// Page p's source-block bitmap: one CTA per page ORs the block of every
+// in-edge source into shared memory, then writes the page's words.
+__global__ void __launch_bounds__(kNT) page_blocks_kernel(const uint32_t* __restrict__ col,
+                                                          const uint64_t* __restrict__ eb,
+                                                          uint32_t bsz, uint32_t* __restrict__ out) {
+    __shared__ uint32_t bits[kPageBlockWords];
+    if (threadIdx.x < kPageBlockWords) bits[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t b = eb[blockIdx.x], e = eb[blockIdx.x + 1];
+    for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const uint32_t blk = col[i] / bsz;
+        atomicOr(&bits[blk >> 5], 1u << (blk & 31));
+    }
+    __syncthreads();
+    if (threadIdx.x < kPageBlockWords) out[(uint64_t)blockIdx.x * kPageBlockWords + threadIdx.x] = bits[threadIdx.x];
+}
+
 __global__ void page_cut_kernel(const uint64_t* __restrict__ col_off, uint64_t n, uint32_t P,
                                 uint64_t* __restrict__ vb) {
     const uint64_t total = n + col_off[n];
@@ -905,6 +922,11 @@ void build_graph(seraph_graph* g, uint64_t n, uint64_t m, const uint32_t* src_in
     DevBuf<uint64_t> d_vb(P + 1), d_eb(P + 1);
     page_cut_kernel<<<grid_for(P + 1), kNT, 0, s>>>(col_off.p, n, P, d_vb.p);
     gather_off_kernel<<<grid_for(P + 1), kNT, 0, s>>>(col_off.p, d_vb.p, P, d_eb.p);
+    SR_LAUNCH();
+    // source blocks of 32-multiple sizes: 32 consecutive ids share a block
+    g->src_block = (uint32_t)align_up((n + 32 * kPageBlockWords - 1) / (32 * kPageBlockWords), 32);
+    g->d_page_blocks.alloc((uint64_t)P * kPageBlockWords);
+    page_blocks_kernel<<<P, kNT, 0, s>>>(col.p, d_eb.p, g->src_block, g->d_page_blocks.p);
     SR_LAUNCH();
     g->vb.resize(P + 1);
     std::vector<uint64_t> eb(P + 1);

@@ -206,7 +206,6 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
              "the push stage is for SSSP, BFS and CC");
     SR_CHECK(!P->push || g->out_edges, SERAPH_EINVAL,
              "the push stage needs a graph built with SERAPH_OUT_EDGES");
-    SR_CHECK(!P->push || !learned, SERAPH_EINVAL, "the push stage needs a fixed schedule");
     SR_CHECK(!P->push || !(P->algo == SERAPH_CC && !g->symmetrized), SERAPH_EINVAL,
              "CC with the push stage needs a symmetrized graph");
     const uint64_t n = g->n;
@@ -368,12 +367,19 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     }
     if (P->pvu == SERAPH_PVU_WEAK) ensure(state, n);
     const bool push_on = P->push != 0;
+    SR_CHECK(P->count_clean <= 1, SERAPH_EINVAL, "count_clean must be 0 or 1");
+    const bool count_clean = P->count_clean != 0 && !is_pr;
+    DevBuf<uint32_t> dirty_blocks;
+    if (count_clean) dirty_blocks.alloc(32);
     const uint64_t big_cap = std::min<uint64_t>(n, g->m / kPushWarpMax + 1);
     DevBuf<PushState> d_ps;
     PinnedBuf h_ps;
-    if (push_on) {
-        ensure(stamp, n); ensure(front0, n); ensure(front1, n); ensure(big, big_cap);
+    if (push_on || count_clean) {
+        ensure(stamp, n);
         SR_CUDA(cudaMemsetAsync(stamp.p, 0, n * sizeof(uint32_t), cs.s));
+    }
+    if (push_on) {
+        ensure(front0, n); ensure(front1, n); ensure(big, big_cap);
         d_ps.alloc(1);
         h_ps.alloc(sizeof(PushState));
     }
@@ -410,7 +416,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     a.wbytes = (uint8_t)g->wbytes;
     a.packed = packed;
     a.n = (uint32_t)n;
-    a.chg_stamp = push_on ? stamp.p : nullptr;
+    a.chg_stamp = push_on || count_clean ? stamp.p : nullptr;
     a.chg_tag = 1;
     {
         uint64_t hot_bytes = P->l2_hot_bytes;
@@ -746,8 +752,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         if (is_pr)
             launch_close_pr(a, n, x_prev.p, P->damping, partial.p, nparts, d_rep.p,
                             P->pr_normalize != 0, cs.s);
-        else
+        else {
+            if (count_clean) {
+                launch_count_clean(stamp.p, n, S.sweeps + 1, g->src_block, g->d_page_blocks.p,
+                                   g->num_pages, dirty_blocks.p, rs.p, cs.s);
+                launches += 2;
+            }
             launch_close_min(rs.p, d_rep.p, cs.s);
+        }
         launches += is_pr ? (P->pr_normalize ? 4 : 2) : 1;
         SR_CUDA(cudaMemcpyAsync(h_rep.p, d_rep.p, sizeof(SweepReport), cudaMemcpyDeviceToHost, cs.s));
         SR_CUDA(cudaMemcpyAsync(h_steps.p, d_steps.p, ring * sizeof(unsigned), cudaMemcpyDeviceToHost, cs.s));
@@ -776,7 +788,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
                 for (uint32_t c : window_of[s % ring]) proc_step[c] = (int64_t)s;
             // every vertex of the chunk relaxed or final (for the push stage);
             // strong skips count as final where every sweep visits every chunk
-            if (!pred_in_step[s % ring] || (P->pvu == SERAPH_PVU_STRONG && !zig))
+            // (not zigzag; the learned mode skips chunks only with verify = 1)
+            if (!pred_in_step[s % ring] ||
+                (P->pvu == SERAPH_PVU_STRONG && !zig && !(learned && P->verify)))
                 for (uint32_t c : window_of[s % ring]) valid_tag[c] = S.sweeps + 1;
         }
         // clear the ring entries of this sweep for reuse
@@ -786,6 +800,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         S.passes_skipped += rep.passes_skipped;
         S.edges_relaxed += rep.edges;
         S.packed_edges += rep.packed_edges;
+        S.clean_pages += rep.clean_pages;
         S.code_bytes += rep.code_bytes;
         S.vertices_attempted += rep.attempted;
         S.vertices_skipped += rep.skipped;

@@ -12,8 +12,10 @@ execution model), against the oracle.
   whole grid walks.
 - An SSSP candidate that overflows during the push stage ends in the same
   SERAPH_EOVERFLOW as without it.
+- It runs under the learned schedule too (every chunk still processed after
+  the switch point's sweeps), bit-exact.
 - Misuse is rejected (PageRank, a graph without out-edges, CC on a directed
-  graph, a learned schedule)."""
+  graph)."""
 import numpy as np
 import pytest
 
@@ -176,10 +178,23 @@ def test_push_misuse_is_rejected(r15):
     g, gs = r15["g"], r15["gs"]
     n, src, dst = r15["n"], r15["src"], r15["dst"]
     plain = seraph.Graph.from_edges(n, src, dst, None, num_pages=4)
-    bad = [(g, "pagerank", {}), (plain, "bfs", {}), (g, "cc", {}),
-           (g, "sssp", dict(sched_model=seraph.SchedModel(), window=1))]
+    bad = [(g, "pagerank", {}), (plain, "bfs", {}), (g, "cc", {})]
     for gg, algo, kw in bad:
         with pytest.raises(seraph.SeraphError) as ei:
             seraph.run(gg, algo, budget_bytes=1 << 24, push=1, **kw)
         assert ei.value.code == C.SERAPH_EINVAL, (algo, kw)
     plain.free()
+
+
+def test_push_under_the_learned_schedule(r15):
+    g, ref = r15["g"], r15["ref"]
+    from paper_1806_00762_b300 import train_sched
+    model = seraph.SchedModel()
+    params = train_sched.load()
+    if params is not None:
+        model.set_params(params)
+    for verify, pvu in ((0, "strong"), (1, "strong"), (1, "off")):
+        got, st = seraph.run(g, "sssp", source=0, window=1, slots=6, pvu=pvu, verify=verify,
+                             budget_bytes=6 * (slot_bytes(g) + 256), sched_model=model, max_passes=4,
+                             push=1, push_below=2000)
+        assert np.array_equal(got, ref[("sssp", 0)]), (verify, pvu)
