@@ -640,6 +640,9 @@ def main():
                 "time_to_fixpoint_s": learned_t,
                 "sweeps": {"sssp": l1["sweeps"], "pagerank": l2["sweeps"]},
                 "fixed_time_to_fixpoint_s": fixed_t,
+                # the method without the network: the paper's fixed k = 4 pipeline
+                "fixed_k4_time_to_fixpoint_s": (line["paper_schedule"]["time_to_fixpoint_s"]
+                                                if "paper_schedule" in line else None),
                 "gteps": 2 * E / (sum(learned_t.values())) / 1e9,
                 # the fixed schedule is the yardstick: keep the learned one only where it wins
                 "chosen": {a: ("learned" if learned_t[a] < fixed_t[a] else "fixed") for a in fixed_t},

@@ -439,12 +439,14 @@ int seraph_gather_probe(uint64_t n_values, uint64_t n_gathers, uint64_t hot_valu
  * number of local passes k in [1,16] for the step (argmax of 16 logits) and a
  * streaming priority (predicted first-pass gain).  With params.sched =
  * SERAPH_SCHED_LEARNED (window must be 1) the device caps each step's passes
- * at the predicted k (no host round trip) and sweeps keep the base chunk
- * order (cyclic or zigzag); for SSSP/BFS/CC a chunk predicted to change
- * nothing (priority < 0.02) may be skipped, for at most three sweeps in a
- * row and never when verify = 0, which the stop rule (every chunk processed
- * after the last change) makes safe.  The fixed schedule remains the
- * fallback and the yardstick.
+ * at the predicted k (no host round trip).  For SSSP/BFS/CC the priority
+ * orders the stream: each sweep takes the chunks already in the ring first,
+ * then the others, each group by decreasing predicted gain (PageRank keeps
+ * the base cyclic or zigzag order); a chunk predicted to change nothing
+ * (priority < 0.02) may be skipped, for at most three sweeps in a row and
+ * never when verify = 0, which the stop rule (every chunk processed after the
+ * last change) makes safe.  The fixed schedule remains the fallback and the
+ * yardstick.
  */
 #define SERAPH_SCHED_FEATURES 16
 #define SERAPH_SCHED_OUTPUTS 17

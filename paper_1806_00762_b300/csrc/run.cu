@@ -909,11 +909,21 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             if (!stop && S.sweeps >= P->max_sweeps) { rc = SERAPH_ENOTCONV; stop = true; }
         }
         if (stop) break;
-        if (learned) {  // the next sweep: the base order without chunks predicted idle
+        if (learned) {  // the next sweep's order, without chunks predicted idle
             const float* pr = (const float*)h_prio.p;
             std::vector<uint32_t> ord(C);
             std::iota(ord.begin(), ord.end(), 0u);
             if (zig_base && (S.sweeps & 1)) std::reverse(ord.begin(), ord.end());
+            // SSSP/BFS/CC stream the chunks in order of predicted gain, the
+            // chunks already in the ring first (they cost no copy), so that the
+            // largest improvements propagate through the rest of the sweep;
+            // PageRank keeps the base order (forward Gauss-Seidel blocks)
+            if (!is_pr)
+                std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
+                    const bool rx = slot_of[x] >= 0, ry = slot_of[y] >= 0;
+                    if (rx != ry) return rx;
+                    return pr[x] > pr[y];
+                });
             // SSSP/BFS/CC: skip chunks predicted to change nothing, except after
             // a sweep without changes and at least every fourth sweep (the
             // stop rule needs every chunk processed after the last change)

@@ -2,9 +2,14 @@
 
 Traces come from SSSP, BFS and PageRank runs on seeded R-MAT graphs built as
 the benchmark builds them (out-degree order, hybrid pages; PageRank with the
-unit-sum scaling and over-relaxed steps), at scale 24 with small ring slots
-and at scale 28 with the benchmark's rings, each step running up to 16 local
-passes so that the gain of every extra pass is seen.
+unit-sum scaling and over-relaxed steps), each step running up to 16 local
+passes so that the gain of every extra pass is seen:
+- scale 24, 1024 pages, a ring of 64 slots under a 256 MB budget (every
+  sweep streams hundreds of chunks): SSSP (hybrid pages from 32 seeded
+  sources with an out-edge, plain pages from 16) and BFS from 16, PageRank
+  with over-relaxation 1, 1.15 and 1.3 -- most of the rows;
+- scale 24 with a 2 GB ring (resident after one sweep), a few runs;
+- scale 28 with the benchmark's rings (SSSP 16 slots, PageRank 14).
 Targets (seraph_sched_targets): k = fewest passes holding 95 % of a step's
 changes, priority = log2(1 + first-pass changes) / 24.  Training uses the
 library's own forward/backward/Adam kernels.  The FP32 master weights are
@@ -49,11 +54,14 @@ def collect(seraph, torch, g, budget, runs):
         tr = seraph.TraceBuffer(500_000)
         out = torch.empty(n, dtype=torch.float32 if algo == "pagerank" else torch.int32,
                           device="cuda")
-        # the benchmark's page form: hybrid (leading pages packed, the rest plain)
+        # the benchmark's page form unless a run says otherwise: hybrid
+        # (leading pages packed, the rest plain)
+        kw = dict(dict(columns="hybrid"), **extra)
         seraph.run(g, algo, out=out, source=source, window=1, slots=slots, passes=16, trace=tr,
-                   budget_bytes=budget, columns="hybrid", **extra)
+                   budget_bytes=budget, **kw)
         f, _, _ = tr.rows()
         k, p = tr.targets(0.95)
+        print(f"trace {algo} source {source} slots {slots} {extra}: {len(k)} rows", flush=True)
         xs.append(f.copy())
         ks.append(k)
         ps.append(p)
@@ -85,9 +93,25 @@ def main():
         # default) and steps over-relaxed by 1.15
         pr = {"pr_omega": 1.15}
         if scale <= 24:
-            g = _graph(seraph, synth, torch, scale, 256)
-            runs = ([("sssp", s, 64, {}) for s in (0, 12345, 99, 777, 4242, 31337)] +
-                    [("pagerank", 0, 64, pr), ("bfs", 0, 64, {}), ("bfs", 12345, 64, {})])
+            g = _graph(seraph, synth, torch, scale, 1024)
+            n = 1 << scale
+            # sources among the vertices with an out-edge (in the caller's ids)
+            _, _, _, outdeg = g.export_csc()
+            has_out = np.zeros(n, dtype=bool)
+            has_out[g.perm()[outdeg > 0]] = True
+            srcs = [0] + synth.pick_sources(n, has_out, 31, seed=11)
+            # streamed: 1024 pages through a ring of 64 slots (hundreds of chunks)
+            plain = {"columns": "plain"}
+            runs = ([("sssp", s, 64, {}) for s in srcs] + [("sssp", s, 64, plain) for s in srcs[:16]] +
+                    [("bfs", s, 64, {}) for s in srcs[:16]] +
+                    [("pagerank", 0, 64, pr), ("pagerank", 0, 64, dict(pr, **plain)),
+                     ("pagerank", 0, 64, {"pr_omega": 1.0}), ("pagerank", 0, 64, {"pr_omega": 1.3})])
+            x, k, p = collect(seraph, torch, g, 256 << 20, runs)
+            xs += x
+            ks += k
+            ps += p
+            # resident after one sweep
+            runs = ([("sssp", s, 64, {}) for s in srcs[:4]] + [("pagerank", 0, 64, pr)])
             x, k, p = collect(seraph, torch, g, 2 << 30, runs)
         else:
             g = _graph(seraph, synth, torch, scale, 512)
