@@ -168,10 +168,14 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True,
     return g
 
 
-# DRAM traffic of the relax kernels per launch on this workload, from one ncu
-# capture of the default step (profiles/launches_rmat28_sssp_pagerank.md);
-# valid only for the kernel source and the two schedules it was taken on.
-RELAX_TRAFFIC = {"engine_sha256": "12bf6fac3d30c341", "bytes_per_launch": 5.220801756e9,
+# DRAM traffic of the relax kernels per launch on this workload, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass) on six launches of
+# the default step at full size -- three PageRank launches (plain columns, the
+# resident sweeps) and three SSSP launches (packed columns, the resident
+# sweeps) -- weighted by the step's 154 PageRank and 64 SSSP relax launches
+# (profiles/relax_kernel_dram_rmat28.md); valid only for the kernel source and
+# the two schedules it was taken on.
+RELAX_TRAFFIC = {"engine_sha256": "927d5f397eb0d637", "bytes_per_launch": 6.4188e9,
                  "sssp": "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid,push=1",
                  "pagerank": "order=zigzag,window=1,slots=14,pvu=weak,columns=hybrid,"
                              "pr_normalize=1,pr_omega=1.15",
