@@ -41,8 +41,10 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-fixpoint and effective GTEPS, RMAT-28 streamed; learned vs fixed sched"
 
 
-DEFAULT_SSSP = "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid,push=1"
-DEFAULT_PAGERANK = "order=zigzag,window=1,slots=14,pvu=weak,columns=hybrid,pr_normalize=1,pr_omega=1.15"
+DEFAULT_SSSP = ("order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid,push=1,"
+                "stream_packed=1")
+DEFAULT_PAGERANK = ("order=zigzag,window=1,slots=14,pvu=weak,columns=hybrid,pr_normalize=1,"
+                    "pr_omega=1.15,stream_packed=1")
 
 
 def parse():
@@ -176,9 +178,8 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True,
 # (profiles/relax_kernel_dram_rmat28.md); valid only for the kernel source and
 # the two schedules it was taken on.
 RELAX_TRAFFIC = {"engine_sha256": "927d5f397eb0d637", "bytes_per_launch": 6.4188e9,
-                 "sssp": "order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid,push=1",
-                 "pagerank": "order=zigzag,window=1,slots=14,pvu=weak,columns=hybrid,"
-                             "pr_normalize=1,pr_omega=1.15",
+                 "sssp": DEFAULT_SSSP,
+                 "pagerank": DEFAULT_PAGERANK,
                  "workload": "rmat28 default step"}
 
 

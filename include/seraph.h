@@ -312,7 +312,18 @@ typedef struct seraph_params {
                                    sources are grouped in 1024 blocks of
                                    consecutive ids, so the count is a lower
                                    bound                                     */
-    uint32_t pad3;
+    uint32_t stream_packed;     /* 1 (graphs built with SERAPH_COMPRESS): a
+                                   chunk processed in the plain form streams
+                                   in its packed form into the far end of its
+                                   ring slot and is decoded on the device into
+                                   the plain form, page by page (each page's
+                                   plain bytes end before its packed bytes
+                                   start), so the host link carries the packed
+                                   bytes; chunks that cannot be laid out so
+                                   stream plain.  Chunks are cut with one
+                                   packed page of slack.  A transfer encoding
+                                   (not in the paper): results unchanged.
+                                   0 = off                                   */
 } seraph_params;
 
 #define SERAPH_L2_HOT_AUTO UINT64_MAX

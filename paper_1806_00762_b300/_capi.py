@@ -67,7 +67,7 @@ class Params(ctypes.Structure):
                 ("group8_max_deg", u32),
                 ("sched_model", vp), ("stream", vp), ("trace", vp), ("columns", u32),
                 ("pad1", u32), ("l2_hot_bytes", u64), ("pr_omega", dbl), ("push", u32),
-                ("pad2", u32), ("push_below", u64), ("count_clean", u32), ("pad3", u32)]
+                ("pad2", u32), ("push_below", u64), ("count_clean", u32), ("stream_packed", u32)]
 
 
 class Stats(ctypes.Structure):

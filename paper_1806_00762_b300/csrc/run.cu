@@ -44,6 +44,10 @@ struct Chunk {
     uint64_t w_slot_off;        // weights start this far into the slot
     uint32_t v_begin, v_end;
     bool packed;                // pages in the packed form (else plain)
+    // stream_packed: the plain chunk streams its packed bytes [pk_begin,
+    // pk_begin + pk_bytes) to slot offset stage_off and is decoded in place
+    bool decode;
+    uint64_t pk_begin, pk_bytes, stage_off;
 };
 
 struct Event {
@@ -223,6 +227,10 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
                             (P->columns != SERAPH_COLUMNS_AUTO || g->packed);
     SR_CHECK(!any_packed || g->packed, SERAPH_EINVAL, "graph was built without SERAPH_COMPRESS");
     const bool hybrid = P->columns == SERAPH_COLUMNS_HYBRID;
+    SR_CHECK(P->stream_packed <= 1, SERAPH_EINVAL, "stream_packed must be 0 or 1");
+    const bool stream_packed = P->stream_packed != 0;
+    SR_CHECK(!stream_packed || g->packed, SERAPH_EINVAL,
+             "stream_packed needs a graph built with SERAPH_COMPRESS");
     SR_CHECK(!hybrid || P->window == 1, SERAPH_EINVAL, "hybrid page forms need window = 1");
     const uint32_t W = P->window;
     const uint32_t R = P->slots ? P->slots : W + 1;
@@ -242,13 +250,17 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             const bool pk = p < npk;
             const uint64_t sb = pk ? pm.pk_bytes : pm.s_bytes;
             const uint64_t wb = use_w ? pm.w_bytes : 0;
+            // a plain page that may stream packed leaves room for its packed
+            // form behind the chunk's plain bytes (the decode's staging)
+            const uint64_t slack = stream_packed && !pk ? align_up(pm.pk_bytes, 256) : 0;
             if (align_up(sb, 256) + wb > slot_bytes) {
                 SR_CHECK(!strict, SERAPH_EBUDGET,
                          "page " + std::to_string(p) + " (" + std::to_string(sb + wb) +
                              " B) does not fit a ring slot of " + std::to_string(slot_bytes) + " B");
                 return false;
             }
-            if (open && cur.packed == pk && align_up(cur.s_bytes + sb, 256) + cur.w_bytes + wb <= slot_bytes) {
+            if (open && cur.packed == pk &&
+                align_up(cur.s_bytes + sb, 256) + cur.w_bytes + wb + slack <= slot_bytes) {
                 cur.end_page = p + 1;
                 cur.s_bytes += sb;
                 cur.w_bytes += wb;
@@ -257,7 +269,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             }
             if (open) out.push_back(cur);
             cur = Chunk{p, p + 1, pk ? pm.pk_off : pm.s_off, sb, pm.w_off, wb, 0, (uint32_t)pm.vb,
-                        (uint32_t)(pm.vb + pm.nv), pk};
+                        (uint32_t)(pm.vb + pm.nv), pk, false, 0, 0, 0};
             open = true;
         }
         if (open) out.push_back(cur);
@@ -280,6 +292,24 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     make_chunks(npk, chunks, true);
     const bool packed = npk > 0;  // some pages stream packed
     for (auto& c : chunks) c.w_slot_off = align_up(c.s_bytes, 256);
+    // Streaming a plain chunk packed: its packed pages go to the far end of
+    // the slot and page j is decoded into its plain place, which must end
+    // before page j's packed bytes start (pages are decoded in order, so an
+    // earlier page's packed bytes may be overwritten once decoded).
+    for (auto& c : chunks) {
+        if (!stream_packed || c.packed) continue;
+        c.pk_begin = g->pages[c.first_page].pk_off;
+        const PageMeta& last = g->pages[c.end_page - 1];
+        c.pk_bytes = last.pk_off + last.pk_bytes - c.pk_begin;
+        if (c.pk_bytes >= c.s_bytes || c.pk_bytes > slot_bytes) continue;
+        c.stage_off = (slot_bytes - c.pk_bytes) & ~255ull;
+        bool fits = true;
+        for (uint32_t p = c.first_page; p < c.end_page && fits; ++p) {
+            const PageMeta& pm = g->pages[p];
+            fits = (pm.s_off - c.s_begin) + pm.s_bytes <= c.stage_off + (pm.pk_off - c.pk_begin);
+        }
+        c.decode = fits;
+    }
     const uint32_t C = (uint32_t)chunks.size();
     const bool resident = C <= R;
     const uint32_t Weff = W < C ? W : C;
@@ -306,9 +336,10 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     while (ring < 4 * (uint64_t)C + 8) ring <<= 1;
 
     // --------------------------------------------------------- allocations
-    Stream cs, xs;
+    Stream cs, xs, ds;  // compute, copies, decode of packed-streamed chunks
     cs.use(P->stream);
     xs.create();
+    if (stream_packed) ds.create();
     DevBuf<uint8_t> ebuf;
     DevBuf<unsigned long long> lists;
     DevBuf<uint32_t> val, caller_order;
@@ -453,10 +484,12 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     }
 
     // -------------------------------------------------------------- events
-    std::vector<Event> step_done(ring), copy_done(C);
+    std::vector<Event> step_done(ring), copy_done(C), staged(C);
     std::vector<uint32_t> npass_of(ring, 0);
     for (auto& e : step_done) e.create(false);
     for (auto& e : copy_done) e.create(false);
+    for (uint32_t c = 0; c < C; ++c)
+        if (chunks[c].decode) staged[c].create(false);
     Event ev_start, ev_stop, ev_sweep;
     ev_start.create(true);
     ev_stop.create(true);
@@ -562,25 +595,51 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     };
 
     // copy chunk c into `slot` on the copy stream, during step t
+    // chunk last loaded into each slot: a decode on the side stream may still
+    // be writing it when the slot is reloaded without a step having used it
+    std::vector<int64_t> slot_load(nslots, -1);
     auto load = [&](uint32_t c, int64_t slot, uint64_t t) {
         if (last_use[slot] >= 0) SR_CUDA(cudaStreamWaitEvent(xs.s, step_done[last_use[slot] % ring].e, 0));
+        if (slot_load[slot] >= 0 && chunks[slot_load[slot]].decode)
+            SR_CUDA(cudaStreamWaitEvent(xs.s, copy_done[slot_load[slot]].e, 0));
         const Chunk& ch = chunks[c];
         uint8_t* sb = ebuf.p + (uint64_t)slot * slot_bytes;
         if (prof) SR_CUDA(cudaEventRecord(pc_b[(load_seq + 1) % ring].e, xs.s));
-        SR_CUDA(cudaMemcpyAsync(sb, (ch.packed ? g->h_pack.p : g->h_struct.p) + ch.s_begin, ch.s_bytes,
-                                cudaMemcpyHostToDevice, xs.s));
+        cudaStream_t fin = xs.s;  // the stream that finishes the load
+        if (ch.decode) {
+            // packed bytes to the far end of the slot, then (on the decode
+            // stream, so the copy engine moves on to the next chunk) each page
+            // decoded into its plain place, in page order
+            SR_CUDA(cudaMemcpyAsync(sb + ch.stage_off, g->h_pack.p + ch.pk_begin, ch.pk_bytes,
+                                    cudaMemcpyHostToDevice, xs.s));
+            SR_CUDA(cudaEventRecord(staged[c].e, xs.s));
+            SR_CUDA(cudaStreamWaitEvent(ds.s, staged[c].e, 0));
+            fin = ds.s;
+            for (uint32_t p = ch.first_page; p < ch.end_page; ++p) {
+                const PageMeta& pm = g->pages[p];
+                launch_decode_page(sb + ch.stage_off + (pm.pk_off - ch.pk_begin),
+                                   sb + (pm.s_off - ch.s_begin), (uint32_t)pm.nv, pm.off_bytes,
+                                   pm.s_bytes, ds.s);
+                ++launches;
+            }
+        } else {
+            SR_CUDA(cudaMemcpyAsync(sb, (ch.packed ? g->h_pack.p : g->h_struct.p) + ch.s_begin,
+                                    ch.s_bytes, cudaMemcpyHostToDevice, xs.s));
+        }
+        // weights after the decode (they may overlap the packed staging bytes)
         if (use_w && ch.w_bytes)
             SR_CUDA(cudaMemcpyAsync(sb + ch.w_slot_off, g->h_weight.p + ch.w_begin, ch.w_bytes,
-                                    cudaMemcpyHostToDevice, xs.s));
-        if (prof) SR_CUDA(cudaEventRecord(pc_e[(load_seq + 1) % ring].e, xs.s));
+                                    cudaMemcpyHostToDevice, fin));
+        if (prof) SR_CUDA(cudaEventRecord(pc_e[(load_seq + 1) % ring].e, fin));
         launch_set_locs(loc.p, g->d_vb.p, ch.first_page, ch.end_page, d_rel_soff.p, d_rel_woff.p,
-                        d_offb.p, sb, use_w ? sb : nullptr, ch.packed, rs.p, ++load_seq, xs.s);
+                        d_offb.p, sb, use_w ? sb : nullptr, ch.packed, rs.p, ++load_seq, fin);
         ++launches;
-        SR_CUDA(cudaEventRecord(copy_done[c].e, xs.s));
+        SR_CUDA(cudaEventRecord(copy_done[c].e, fin));
+        slot_load[slot] = (int64_t)c;
         slot_of[c] = slot;
         chunk_in[slot] = c;
         pending[c] = 1;
-        S.bytes_streamed += ch.s_bytes + (use_w ? ch.w_bytes : 0);
+        S.bytes_streamed += (ch.decode ? ch.pk_bytes : ch.s_bytes) + (use_w ? ch.w_bytes : 0);
     };
 
     const unsigned relax_grid = device_sms() * 8;
@@ -964,6 +1023,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     }
     SR_CUDA(cudaStreamSynchronize(cs.s));
     SR_CUDA(cudaStreamSynchronize(xs.s));
+    if (stream_packed) SR_CUDA(cudaStreamSynchronize(ds.s));
     S.kernel_launches = launches;
     S.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     if (st) *st = S;

@@ -18,7 +18,7 @@ def test_parse_sched_types_and_defaults():
     assert pr["pr_omega"] == 1.15 and pr["pr_normalize"] == 1
     ss = bench.parse_sched(bench.DEFAULT_SSSP)
     assert ss == dict(order="cyclic", window=1, slots=16, pvu="strong", verify=0, columns="hybrid",
-                      push=1)
+                      push=1, stream_packed=1)
     assert bench.parse_sched("") == {}
 
 
