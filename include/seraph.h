@@ -545,7 +545,18 @@ typedef struct seraph_batch_params {
                                    bottom-up -- every unvisited vertex looks
                                    for a parent among its in-neighbours --
                                    instead of pushing (0 = 5; 1 = never)     */
-    uint32_t reserved2;
+    uint32_t group;             /* 1 (default): queries of one graph and one
+                                   algorithm run in lockstep groups of up to
+                                   8 -- one frontier of vertices for the
+                                   group, per vertex the sub-queries that
+                                   hold it, distances interleaved -- so one
+                                   read of a vertex's out-edges serves every
+                                   sub-query that holds it and a
+                                   destination's distances share one sector
+                                   (the group shares the near-far split; edge-
+                                   balanced CTA tiles of at most 512 vertices
+                                   whatever the mapping).  Exact distances
+                                   either way.  0 = one record per query     */
 } seraph_batch_params;
 
 typedef struct seraph_batch_stats {

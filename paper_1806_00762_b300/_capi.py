@@ -101,7 +101,7 @@ class Query(ctypes.Structure):
 class BatchParams(ctypes.Structure):
     _fields_ = [("mapping", i32), ("tile", u32), ("use_graph", u32), ("replays", u32),
                 ("timeout_ms", u32), ("delta", u32), ("stream", vp), ("bfs_pull_div", u32),
-                ("reserved2", u32)]
+                ("group", u32)]
 
 
 class BatchStats(ctypes.Structure):

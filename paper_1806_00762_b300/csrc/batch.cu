@@ -49,6 +49,19 @@ struct BGraphDev {
 // split to (smallest far distance) + delta and moves the far vertices now
 // below it to the near frontier, keeping the rest in the other far pile.
 // BFS queries keep split = infinity (plain level-synchronous push).
+//
+// A record may also run a group of up to kMaxGroup queries of one graph and
+// one algorithm in lockstep (gsz > 1): distances interleaved (dist[v * gsz +
+// j] for sub-query j), one frontier of vertices for all of them, and per
+// vertex a word (round << 8 | sub-query bits) telling which sub-queries hold
+// it in the frontier of a round (mword, double-buffered by round parity) or
+// in a far pile of an epoch (fword).  One read of a frontier vertex's
+// out-edges then serves every sub-query that holds it, and the sub-queries'
+// distances of a destination share one 32-byte sector.  The group shares
+// one near-far split.
+constexpr uint32_t kMaxGroup = 8;
+constexpr uint32_t kMaxGroupTile = 512;
+
 struct BQuery {
     uint32_t graph, algo, source, mapping, tile;
     uint32_t round, cur_n, next_n, tiles_total, tiles_done, done, pull_min;
@@ -58,6 +71,17 @@ struct BQuery {
     uint32_t* front[2];
     uint32_t* far[2];
     uint32_t* fstamp;
+    uint32_t gsz;              // sub-queries (1: a single query, the fields above)
+    uint32_t* mword[2];        // group: near-frontier words by round parity
+    uint32_t* fword[2];        // group (SSSP): far-pile words by pile
+};
+
+// A group's sources and per-sub-query outputs (n distances each), read only
+// at the start and the end of a launch.
+struct BGroupIO {
+    uint32_t src[kMaxGroup];
+    uint32_t* gout[kMaxGroup];
+    uint32_t tiles0;           // tiles of round 0 (every record)
 };
 
 constexpr uint32_t kPhaseNear = 0, kPhaseFilter = 1, kPhasePull = 2;
@@ -164,7 +188,30 @@ __device__ __forceinline__ BQuery load_query(const BQuery* p) {
     Q.epoch = v->epoch; Q.far_min = 0; Q.far_n[0] = Q.far_n[1] = 0;
     Q.dist = v->dist; Q.stamp = v->stamp; Q.front[0] = v->front[0]; Q.front[1] = v->front[1];
     Q.far[0] = v->far[0]; Q.far[1] = v->far[1]; Q.fstamp = v->fstamp;
+    Q.gsz = v->gsz;
+    Q.mword[0] = v->mword[0]; Q.mword[1] = v->mword[1];
+    Q.fword[0] = v->fword[0]; Q.fword[1] = v->fword[1];
     return Q;
+}
+
+// Sets `bits` in a (tag << 8 | bits) word for `tag`: a word of an older tag
+// starts over.  Returns true if this call opened the tag (the vertex enters
+// the list of that round or epoch).  Each retry follows another thread's
+// change of the word, and a word changes at most kMaxGroup + 1 times per tag.
+__device__ __forceinline__ bool tag_or(uint32_t* w, uint32_t tag, uint32_t bits) {
+    uint32_t old = *(volatile uint32_t*)w;
+    for (;;) {
+        const bool same = (old >> 8) == tag;
+        const uint32_t want = same ? (old | bits) : ((tag << 8) | bits);
+        if (want == old) return false;
+        const uint32_t prev = atomicCAS(w, old, want);
+        if (prev == old) return !same;
+        old = prev;
+    }
+}
+
+__device__ __forceinline__ uint32_t tag_bits(uint32_t w, uint32_t tag) {
+    return (w >> 8) == tag ? (w & 0xFFu) : 0u;
 }
 
 
@@ -308,17 +355,202 @@ __device__ unsigned long long pull_tile(BQuery* qs, uint32_t q, const BQuery& Q,
     return edges;
 }
 
+// ------------------------------------------------------------ query groups
+
+// Out-edge (u -> v) of weight w for the sub-queries in `bits` (u's distances
+// du[j]): `near` / `far` receive the sub-queries it improved below / at or
+// above the group's split.
+__device__ __forceinline__ void group_relax(const BQuery& Q, uint32_t v, uint32_t w, uint32_t bits,
+                                            const uint32_t* du, uint32_t& near, uint32_t& far) {
+    near = far = 0;
+    uint32_t* row = Q.dist + (uint64_t)v * Q.gsz;
+    for (uint32_t m = bits; m; m &= m - 1) {
+        const uint32_t j = __ffs(m) - 1;
+        const uint32_t d = du[j];
+        if (d == SERAPH_INF) continue;
+        const uint32_t c = d + (Q.algo == SERAPH_SSSP ? w : 1u);
+        if (c < d || c == SERAPH_INF) continue;  // overflowing candidates are dropped
+        if (c >= __ldcg(row + j)) continue;
+        if (c >= atomicMin(row + j, c)) continue;
+        if (c < Q.split) near |= 1u << j;
+        else far |= 1u << j;
+    }
+}
+
+// A group's frontier tile, edge-balanced over the CTA like the CTA mapping of
+// single queries (parts of kPartEdges edges included): each frontier vertex
+// brings its sub-query bits and distances, each edge is read once for all
+// of them.
+__device__ unsigned long long group_near_tile(const BGraphDev& G, BQuery* qs, uint32_t q,
+                                              const BQuery& Q, uint32_t tile, uint32_t part,
+                                              const RingCtx& rc, uint64_t* s_pref, uint64_t* s_e0,
+                                              uint32_t* s_gdu, uint32_t* s_gm) {
+    __shared__ uint64_t ws[kNT / 32 + 1];
+    const uint32_t GS = Q.gsz;
+    const uint32_t* cur = Q.front[Q.round & 1];
+    const uint32_t* mw = Q.mword[Q.round & 1];
+    uint32_t* mw_next = Q.mword[(Q.round + 1) & 1];
+    uint32_t* fw = Q.fword[Q.fsel];
+    const uint32_t t0 = tile * Q.tile;
+    const uint32_t cnt = min(Q.tile, Q.cur_n - t0);
+    for (uint32_t base = 0; base < cnt; base += kNT) {
+        const uint32_t i = base + threadIdx.x;
+        uint64_t d = 0;
+        if (i < cnt) {
+            const uint32_t u = __ldcg(cur + t0 + i);
+            const uint64_t b = G.off[u];
+            s_e0[i] = b;
+            s_gm[i] = tag_bits(__ldcg(mw + u), Q.round);
+            for (uint32_t j = 0; j < GS; ++j) s_gdu[i * kMaxGroup + j] = __ldcg(Q.dist + (uint64_t)u * GS + j);
+            d = G.off[u + 1] - b;
+        }
+        uint64_t tot;
+        const uint64_t ex = block_excl_scan<kNT>(d, ws, &tot);
+        const uint64_t run = base ? s_pref[base] : 0;
+        if (i < cnt) s_pref[i] = run + ex;
+        if (threadIdx.x == 0) s_pref[min(base + kNT, cnt)] = run + tot;
+        __syncthreads();
+    }
+    const uint64_t total = s_pref[cnt];
+    const uint64_t lo = (uint64_t)part * kPartEdges;
+    const uint64_t hi = total < lo + kPartEdges ? total : lo + kPartEdges;
+    if (part == 0 && total > kPartEdges) {  // spawn parts 1.. of this tile
+        __shared__ unsigned long long s_t0;
+        __shared__ uint32_t s_n;
+        if (threadIdx.x == 0) {
+            s_n = (uint32_t)((total - 1) / kPartEdges);
+            atomicAdd(&qs[q].tiles_total, s_n);  // before this task counts as done
+            s_t0 = atomicAdd(&rc.gl->tail, (unsigned long long)s_n);
+            atomicAdd(&rc.gl->tasks, (unsigned long long)s_n);
+        }
+        __syncthreads();
+        if (!publish(rc.ring, rc.mask, s_t0, s_n, q, rc.spin_limit, true, tile))
+            atomicOr(&rc.gl->err, 4u);
+        __syncthreads();
+    }
+    for (uint64_t k0 = lo; k0 < hi; k0 += (uint64_t)kNT * kEdgeIlp) {
+        int pn[kEdgeIlp], pf[kEdgeIlp];
+        uint32_t vv[kEdgeIlp];
+#pragma unroll
+        for (int j = 0; j < kEdgeIlp; ++j) {
+            const uint64_t k = k0 + (uint64_t)j * kNT + threadIdx.x;
+            pn[j] = pf[j] = kPushNone;
+            vv[j] = 0;
+            if (k < hi) {
+                uint32_t a = 0, z = cnt - 1;  // largest i with s_pref[i] <= k
+                while (a < z) {
+                    const uint32_t mid = (a + z + 1) >> 1;
+                    if (s_pref[mid] <= k) a = mid; else z = mid - 1;
+                }
+                const uint64_t e = s_e0[a] + (k - s_pref[a]);
+                const uint32_t v = G.col[e];
+                uint32_t near, far;
+                group_relax(Q, v, weight_at(G, e), s_gm[a], s_gdu + a * kMaxGroup, near, far);
+                vv[j] = v;
+                if (near && tag_or(mw_next + v, Q.round + 1, near)) pn[j] = kPushNear;
+                if (far && tag_or(fw + v, Q.epoch + 1, far)) pf[j] = kPushFar;
+            }
+        }
+        append_block(qs, q, Q, pn, vv);
+        append_block(qs, q, Q, pf, vv);
+    }
+    __syncthreads();
+    return threadIdx.x == 0 ? hi - lo : 0;
+}
+
+// A group's filter task over far-pile entries [t0, t0 + cnt): each entry's
+// sub-queries now below the split join the near frontier, the others the
+// other far pile.
+__device__ void group_filter_tile(BQuery* qs, uint32_t q, const BQuery& Q, uint32_t t0, uint32_t cnt) {
+    const uint32_t* src = Q.far[Q.fsel];
+    const uint32_t dst = Q.fsel ^ 1u, GS = Q.gsz;
+    for (uint32_t base = 0; base < cnt; base += kNT) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t v = 0, fmin = SERAPH_INF;
+        bool pn = false, pf = false;
+        if (i < cnt) {
+            v = __ldcg(src + t0 + i);
+            const uint32_t bits = tag_bits(__ldcg(Q.fword[Q.fsel] + v), Q.epoch);
+            uint32_t near = 0, far = 0;
+            for (uint32_t m = bits; m; m &= m - 1) {
+                const uint32_t j = __ffs(m) - 1;
+                const uint32_t d = __ldcg(Q.dist + (uint64_t)v * GS + j);
+                if (d < Q.split) {
+                    near |= 1u << j;
+                } else {
+                    far |= 1u << j;
+                    fmin = min(fmin, d);
+                }
+            }
+            pn = near && tag_or(Q.mword[(Q.round + 1) & 1] + v, Q.round + 1, near);
+            pf = far && tag_or(Q.fword[dst] + v, Q.epoch + 1, far);
+        }
+        append(Q.front[(Q.round + 1) & 1], &qs[q].next_n, pn, v);
+        append(Q.far[dst], &qs[q].far_n[dst], pf, v);
+        const uint32_t mn = __reduce_min_sync(kFull, fmin);
+        if (lane_id() == 0 && mn != SERAPH_INF) atomicMin(&qs[q].far_min, mn);
+    }
+}
+
+// A group's bottom-up BFS task over vertices [t0, t0 + cnt): a vertex still
+// unvisited by some sub-queries scans its in-neighbours for ones at level
+// `round` in those sub-queries, and stops once it found all of them.
+__device__ unsigned long long group_pull_tile(BQuery* qs, uint32_t q, const BQuery& Q,
+                                              const BGraphDev& G, uint32_t t0, uint32_t cnt) {
+    const uint32_t GS = Q.gsz, r = Q.round;
+    uint32_t* mw_next = Q.mword[(r + 1) & 1];
+    unsigned long long edges = 0;
+    for (uint32_t base = 0; base < cnt; base += kNT) {
+        const uint32_t v = t0 + base + threadIdx.x;
+        uint32_t found = 0;
+        if (base + threadIdx.x < cnt) {
+            uint32_t need = 0;
+            for (uint32_t j = 0; j < GS; ++j)
+                if (__ldcg(Q.dist + (uint64_t)v * GS + j) == SERAPH_INF) need |= 1u << j;
+            if (need) {
+                const uint64_t b = G.in_off[v], e = G.in_off[v + 1];
+                for (uint64_t k = b; k < e && need; ++k) {
+                    ++edges;
+                    const uint32_t u = G.in_col[k];
+                    for (uint32_t m = need; m; m &= m - 1) {
+                        const uint32_t j = __ffs(m) - 1;
+                        if (__ldcg(Q.dist + (uint64_t)u * GS + j) == r) found |= 1u << j;
+                    }
+                    need &= ~found;
+                }
+                for (uint32_t m = found; m; m &= m - 1)
+                    Q.dist[(uint64_t)v * GS + (__ffs(m) - 1)] = r + 1;
+                if (found) mw_next[v] = ((r + 1) << 8) | found;
+            }
+        }
+        append(Q.front[(r + 1) & 1], &qs[q].next_n, found != 0, v);
+    }
+    return edges;
+}
+
 // One task: tile `tile` of query q's current frontier.  Returns edges relaxed.
 // Frontier entries and distances are mutable across rounds: read via L2.
 __device__ unsigned long long process_tile(const BGraphDev* graphs, BQuery* qs, uint32_t q,
                                            uint32_t tile, uint32_t part, const RingCtx& rc,
-                                           uint64_t* s_pref, uint64_t* s_e0, uint32_t* s_du) {
+                                           uint64_t* s_pref, uint64_t* s_e0, uint32_t* s_du,
+                                           uint32_t* s_gdu, uint32_t* s_gm) {
     const BQuery Q = load_query(qs + q);
     const BGraphDev G = graphs[Q.graph];
     const uint32_t* cur = Q.front[Q.round & 1];
     const uint32_t t0 = tile * Q.tile;
     const uint32_t cnt = min(Q.tile, Q.cur_n - t0);
     unsigned long long edges = 0;
+    if (Q.gsz > 1) {
+        if (Q.phase == kPhaseFilter) {
+            group_filter_tile(qs, q, Q, t0, cnt);
+            return 0;
+        }
+        if (Q.phase == kPhasePull) {
+            const uint32_t p0 = tile * kPullTile;
+            return group_pull_tile(qs, q, Q, G, p0, min(kPullTile, G.n - p0));
+        }
+        return group_near_tile(G, qs, q, Q, tile, part, rc, s_pref, s_e0, s_gdu, s_gm);
+    }
     if (Q.phase == kPhaseFilter) {
         filter_tile(qs, q, Q, t0, cnt);
         return 0;
@@ -445,6 +677,8 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
     __shared__ uint64_t s_pref[kMaxCtaTile + 1];
     __shared__ uint64_t s_e0[kMaxCtaTile];
     __shared__ uint32_t s_du[kMaxCtaTile];
+    __shared__ uint32_t s_gdu[kMaxGroupTile * kMaxGroup];
+    __shared__ uint32_t s_gm[kMaxGroupTile];
     __shared__ uint32_t s_q, s_tile, s_part, s_last, s_count;
     const RingCtx rc{ring, mask, spin_limit, gl};
     __shared__ int s_exit;
@@ -476,7 +710,8 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
         __syncthreads();
         if (s_exit) break;
         const uint32_t q = s_q;
-        const unsigned long long e = process_tile(graphs, qs, q, s_tile, s_part, rc, s_pref, s_e0, s_du);
+        const unsigned long long e = process_tile(graphs, qs, q, s_tile, s_part, rc, s_pref, s_e0, s_du,
+                                                  s_gdu, s_gm);
         atomicAdd(&s_edges, e);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -539,10 +774,20 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BGraphDev* graphs, 
     if (threadIdx.x == 0) atomicAdd(&gl->edges, s_edges);
 }
 
-__global__ void init_dist_kernel(BQuery* qs, const BGraphDev* graphs, uint32_t nq) {
+__global__ void init_dist_kernel(BQuery* qs, const BGroupIO* io, const BGraphDev* graphs, uint32_t nq) {
     for (uint32_t q = blockIdx.y; q < nq; q += gridDim.y) {
         const BQuery Q = qs[q];
         const uint32_t n = graphs[Q.graph].n;
+        if (Q.gsz > 1) {  // interleaved distances; the tag words start empty
+            for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+                for (uint32_t j = 0; j < Q.gsz; ++j)
+                    Q.dist[(uint64_t)v * Q.gsz + j] = v == io[q].src[j] ? 0u : SERAPH_INF;
+                Q.mword[0][v] = 0;
+                Q.mword[1][v] = 0;
+                if (Q.fword[0]) { Q.fword[0][v] = 0; Q.fword[1][v] = 0; }
+            }
+            continue;
+        }
         for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
             Q.dist[v] = v == Q.source ? 0u : SERAPH_INF;
             Q.stamp[v] = 0;
@@ -552,13 +797,17 @@ __global__ void init_dist_kernel(BQuery* qs, const BGraphDev* graphs, uint32_t n
 }
 
 // Round 0 of every query (frontier = its source) and the first nq tasks.
-__global__ void init_queries_kernel(BQuery* qs, uint32_t nq, BGlobal* gl, TaskSlot* ring,
-                                    unsigned long long cap) {
+// Round 0 of every record and its first tasks: init_task[i] = (record, tile)
+// of task i < ntask0 (a group's distinct sources may take several tiles).
+__global__ void init_queries_kernel(BQuery* qs, const BGroupIO* io, uint32_t nq, BGlobal* gl,
+                                    TaskSlot* ring, unsigned long long cap, const uint2* init_task,
+                                    uint32_t ntask0) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cap;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        ring[i].seq = i < nq ? i + 1 : 0;
-        ring[i].q = (uint32_t)i;
-        ring[i].tile = 0;
+        const bool first = i < ntask0;
+        ring[i].seq = first ? i + 1 : 0;
+        ring[i].q = first ? init_task[i].x : 0u;
+        ring[i].tile = first ? init_task[i].y : 0u;
         ring[i].part = 0;
     }
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
@@ -566,7 +815,7 @@ __global__ void init_queries_kernel(BQuery* qs, uint32_t nq, BGlobal* gl, TaskSl
         Q.round = 0;
         Q.cur_n = 1;
         Q.next_n = 0;
-        Q.tiles_total = 1;
+        Q.tiles_total = io[q].tiles0;
         Q.tiles_done = 0;
         Q.done = 0;
         Q.split = Q.algo == SERAPH_SSSP ? Q.delta : SERAPH_INF;
@@ -575,16 +824,38 @@ __global__ void init_queries_kernel(BQuery* qs, uint32_t nq, BGlobal* gl, TaskSl
         Q.epoch = 0;
         Q.far_min = SERAPH_INF;
         Q.far_n[0] = Q.far_n[1] = 0;
-        Q.front[0][0] = Q.source;
+        if (Q.gsz > 1) {  // round 0: the distinct sources, each with its sub-queries
+            uint32_t c = 0;
+            for (uint32_t j = 0; j < Q.gsz; ++j) {
+                const uint32_t s = io[q].src[j], w = Q.mword[0][s];
+                if (!(w & 0xFFu)) Q.front[0][c++] = s;
+                Q.mword[0][s] = w | (1u << j);
+            }
+            Q.cur_n = c;
+        } else {
+            Q.front[0][0] = Q.source;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         gl->head = 0;
-        gl->tail = nq;
+        gl->tail = ntask0;
         gl->edges = 0;
-        gl->tasks = nq;
+        gl->tasks = ntask0;
         gl->active = nq;
         gl->err = 0;
         gl->max_round = 0;
+    }
+}
+
+// Group results out of the interleaved distances into one array per sub-query.
+__global__ void group_scatter_kernel(const BQuery* qs, const BGroupIO* io, const BGraphDev* graphs,
+                                     uint32_t nq) {
+    for (uint32_t q = blockIdx.y; q < nq; q += gridDim.y) {
+        const BQuery& Q = qs[q];
+        if (Q.gsz <= 1) continue;
+        const uint32_t n = graphs[Q.graph].n;
+        for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+            for (uint32_t j = 0; j < Q.gsz; ++j) io[q].gout[j][v] = Q.dist[(uint64_t)v * Q.gsz + j];
     }
 }
 
@@ -619,7 +890,8 @@ void wait_stream(cudaStream_t s, uint32_t timeout_ms) {
 // `use_graph`.  Distances of the last repetition are left in `dist_out[q]`.
 Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vector<QSpec>& qs,
                      bool use_graph, uint32_t replays, uint32_t timeout_ms, cudaStream_t s,
-                     std::vector<uint32_t*>* dist_out, std::vector<DevBuf<uint32_t>>* hold) {
+                     std::vector<uint32_t*>* dist_out, std::vector<DevBuf<uint32_t>>* hold,
+                     bool group = false) {
     const uint32_t nq = (uint32_t)qs.size();
     std::vector<BGraphDev> gd(graphs.size());
     for (size_t i = 0; i < graphs.size(); ++i) {
@@ -627,14 +899,45 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
         gd[i] = BGraphDev{g->adj.off.p, g->adj.col.p, g->weighted ? g->adj.wptr() : nullptr,
                           (uint32_t)g->n, g->adj.wbytes, g->in_adj.off.p, g->in_adj.col.p};
     }
-    std::vector<BQuery> qh(nq);
+    // Records: with `group`, the queries of one graph, algorithm and tuning
+    // (tile, near-far width, pull threshold) run in lockstep groups of up to
+    // kMaxGroup; otherwise (and for a query left alone) one record each.
+    std::vector<std::vector<uint32_t>> recs;
+    {
+        std::vector<uint8_t> taken(nq, 0);
+        for (uint32_t q = 0; q < nq; ++q) {
+            if (taken[q]) continue;
+            std::vector<uint32_t> r{q};
+            taken[q] = 1;
+            for (uint32_t p = q + 1; group && p < nq && r.size() < kMaxGroup; ++p) {
+                const QSpec &a = qs[q], &b = qs[p];
+                if (!taken[p] && a.graph == b.graph && a.algo == b.algo && a.tile == b.tile &&
+                    a.delta == b.delta && a.pull_div == b.pull_div) {
+                    r.push_back(p);
+                    taken[p] = 1;
+                }
+            }
+            recs.push_back(r);
+        }
+    }
+    const uint32_t nr = (uint32_t)recs.size();
+    std::vector<BQuery> qh(nr);
+    std::vector<BGroupIO> ioh(nr);
+    std::vector<uint2> init_tasks;  // (record, tile) of every round-0 task
     // every per-query array comes out of one allocation (one cudaMalloc per
     // call instead of several per query), each array 128-byte aligned
     auto words = [](uint64_t n) { return (n + 31) & ~31ull; };
     uint64_t pool_words = 0;
-    for (const QSpec& Q : qs) {
+    for (const auto& r : recs) {
+        const QSpec& Q = qs[r[0]];
         const uint64_t n = graphs[Q.graph]->n;
-        pool_words += words(n) * ((Q.out ? 0 : 1) + 3 + (Q.algo == SERAPH_SSSP ? 3 : 0));
+        const bool sssp = Q.algo == SERAPH_SSSP;
+        if (r.size() == 1) {
+            pool_words += words(n) * ((Q.out ? 0 : 1) + 3 + (sssp ? 3 : 0));
+        } else {  // distances (n x size), fronts, tag words; outputs per query
+            pool_words += words(n * r.size()) + words(n) * (4 + (sssp ? 4 : 0));
+            for (uint32_t q : r) pool_words += qs[q].out ? 0 : words(n);
+        }
     }
     hold->clear();
     hold->emplace_back(std::max<uint64_t>(pool_words, 1));
@@ -642,45 +945,82 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
     auto carve = [&](uint64_t n) { uint32_t* p = pool; pool += words(n); return p; };
     uint64_t tiles = 0;
     uint32_t max_n = 1;
-    for (uint32_t q = 0; q < nq; ++q) {
-        const QSpec& Q = qs[q];
+    bool any_group = false;
+    for (uint32_t ri = 0; ri < nr; ++ri) {
+        const std::vector<uint32_t>& r = recs[ri];
+        const QSpec& Q = qs[r[0]];
         const uint64_t n = graphs[Q.graph]->n;
         max_n = std::max<uint32_t>(max_n, (uint32_t)n);
         BQuery b{};
         b.graph = Q.graph; b.algo = Q.algo; b.source = Q.source; b.mapping = Q.mapping; b.tile = Q.tile;
-        b.dist = Q.out ? Q.out : carve(n);
-        b.stamp = carve(n);
-        b.front[0] = carve(n);
-        b.front[1] = carve(n);
+        b.gsz = (uint32_t)r.size();
         b.delta = Q.delta ? Q.delta : 1u;
         b.pull_min = (uint32_t)(n / (Q.pull_div ? Q.pull_div : 1u));
-        if (Q.algo == SERAPH_SSSP) {  // far piles and their per-epoch stamps
-            b.far[0] = carve(n);
-            b.far[1] = carve(n);
-            b.fstamp = carve(n);
+        if (b.gsz == 1) {
+            b.dist = Q.out ? Q.out : carve(n);
+            b.stamp = carve(n);
+            b.front[0] = carve(n);
+            b.front[1] = carve(n);
+            if (Q.algo == SERAPH_SSSP) {  // far piles and their per-epoch stamps
+                b.far[0] = carve(n);
+                b.far[1] = carve(n);
+                b.fstamp = carve(n);
+            }
+            if (dist_out) (*dist_out)[r[0]] = b.dist;
+        } else {
+            any_group = true;
+            b.tile = std::min<uint32_t>(Q.tile, kMaxGroupTile);
+            b.dist = carve(n * b.gsz);
+            b.front[0] = carve(n);
+            b.front[1] = carve(n);
+            b.mword[0] = carve(n);
+            b.mword[1] = carve(n);
+            if (Q.algo == SERAPH_SSSP) {
+                b.far[0] = carve(n);
+                b.far[1] = carve(n);
+                b.fword[0] = carve(n);
+                b.fword[1] = carve(n);
+            }
+            std::vector<uint32_t> distinct;
+            for (uint32_t j = 0; j < b.gsz; ++j) {
+                const QSpec& S = qs[r[j]];
+                ioh[ri].src[j] = S.source;
+                ioh[ri].gout[j] = S.out ? S.out : carve(n);
+                if (dist_out) (*dist_out)[r[j]] = ioh[ri].gout[j];
+                if (std::find(distinct.begin(), distinct.end(), S.source) == distinct.end())
+                    distinct.push_back(S.source);
+            }
+            ioh[ri].tiles0 = ((uint32_t)distinct.size() + b.tile - 1) / b.tile;
         }
-        qh[q] = b;
-        tiles += (n + Q.tile - 1) / Q.tile + graphs[Q.graph]->adj.E / kPartEdges + 1;
-        if (dist_out) (*dist_out)[q] = b.dist;
+        if (b.gsz == 1) ioh[ri].tiles0 = 1;
+        for (uint32_t t = 0; t < ioh[ri].tiles0; ++t) init_tasks.push_back(make_uint2(ri, t));
+        qh[ri] = b;
+        tiles += (n + b.tile - 1) / b.tile + graphs[Q.graph]->adj.E / kPartEdges + 1;
     }
     const int sms = device_sms();
     const unsigned blocks = (unsigned)sms * 4;
     unsigned long long cap = 1024;
-    while (cap < tiles + nq + 4ull * blocks + 1024) cap <<= 1;
+    const uint32_t ntask0 = (uint32_t)init_tasks.size();
+    while (cap < tiles + ntask0 + 4ull * blocks + 1024) cap <<= 1;
     DevBuf<BGraphDev> d_g(gd.size());
-    DevBuf<BQuery> d_q(nq);
+    DevBuf<BQuery> d_q(nr);
+    DevBuf<BGroupIO> d_io(nr);
+    DevBuf<uint2> d_t0(ntask0);
     DevBuf<BGlobal> d_gl(1);
     DevBuf<TaskSlot> d_ring(cap);
     SR_CUDA(cudaMemcpyAsync(d_g.p, gd.data(), gd.size() * sizeof(BGraphDev), cudaMemcpyHostToDevice, s));
-    SR_CUDA(cudaMemcpyAsync(d_q.p, qh.data(), nq * sizeof(BQuery), cudaMemcpyHostToDevice, s));
+    SR_CUDA(cudaMemcpyAsync(d_q.p, qh.data(), nr * sizeof(BQuery), cudaMemcpyHostToDevice, s));
+    SR_CUDA(cudaMemcpyAsync(d_io.p, ioh.data(), nr * sizeof(BGroupIO), cudaMemcpyHostToDevice, s));
+    SR_CUDA(cudaMemcpyAsync(d_t0.p, init_tasks.data(), ntask0 * sizeof(uint2), cudaMemcpyHostToDevice, s));
     // ~15 polls per microsecond with the back-off: a limit of timeout_ms
     const unsigned long long spin_limit = (unsigned long long)timeout_ms * 15000ull;
     auto enqueue = [&](cudaStream_t st) {
-        const dim3 ig((max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64, std::min<uint32_t>(nq, 65535));
-        init_dist_kernel<<<ig, 256, 0, st>>>(d_q.p, d_g.p, nq);
+        const dim3 ig((max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64, std::min<uint32_t>(nr, 65535));
+        init_dist_kernel<<<ig, 256, 0, st>>>(d_q.p, d_io.p, d_g.p, nr);
         init_queries_kernel<<<(unsigned)std::min<unsigned long long>((cap + 255) / 256, 4096), 256, 0, st>>>(
-            d_q.p, nq, d_gl.p, d_ring.p, cap);
+            d_q.p, d_io.p, nr, d_gl.p, d_ring.p, cap, d_t0.p, ntask0);
         batch_kernel<<<blocks, kNT, 0, st>>>(d_g.p, d_q.p, d_gl.p, d_ring.p, cap - 1, spin_limit);
+        if (any_group) group_scatter_kernel<<<ig, 256, 0, st>>>(d_q.p, d_io.p, d_g.p, nr);
     };
     Outcome out;
     cudaGraph_t graph = nullptr;
@@ -759,6 +1099,8 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
     const uint32_t delta = P->delta ? P->delta : kDefaultDelta;
     const bool tune_delta = P->delta == 0 && P->mapping == SERAPH_MAP_AUTO;
     const uint32_t pull_div = P->bfs_pull_div ? P->bfs_pull_div : kDefaultPullDiv;
+    SR_CHECK(P->group <= 1, SERAPH_EINVAL, "group must be 0 or 1");
+    const bool group = P->group != 0;
     std::vector<seraph_bgraph*> graphs(graphs_in, graphs_in + ng);
     for (auto* g : graphs) SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
     SR_CUDA(cudaSetDevice(graphs[0]->device));
@@ -788,11 +1130,19 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
         float best = 1e30f;
         uint32_t bm = SERAPH_MAP_CTA, bt = 256;
         if (!sub.empty()) {
-            for (uint32_t mp : {(uint32_t)SERAPH_MAP_THREAD, (uint32_t)SERAPH_MAP_WARP, (uint32_t)SERAPH_MAP_CTA})
-                for (uint32_t tl : {64u, 256u, 1024u}) {
+            // grouped queries take the edge-balanced CTA tiles (of at most 512)
+            const std::vector<uint32_t> maps = group ? std::vector<uint32_t>{SERAPH_MAP_CTA}
+                                                     : std::vector<uint32_t>{SERAPH_MAP_THREAD,
+                                                                             SERAPH_MAP_WARP,
+                                                                             SERAPH_MAP_CTA};
+            const std::vector<uint32_t> tls = group ? std::vector<uint32_t>{64u, 256u, 512u}
+                                                    : std::vector<uint32_t>{64u, 256u, 1024u};
+            for (uint32_t mp : maps)
+                for (uint32_t tl : tls) {
                     for (auto& x : sub) { x.mapping = mp; x.tile = tl; }
                     std::vector<DevBuf<uint32_t>> hold;
-                    const Outcome o = launch_batch(one, sub, false, 2, P->timeout_ms, s.s, nullptr, &hold);
+                    const Outcome o = launch_batch(one, sub, false, 2, P->timeout_ms, s.s, nullptr, &hold,
+                                                   group);
                     if (o.ms < best) { best = o.ms; bm = mp; bt = tl; }
                 }
         }
@@ -806,7 +1156,7 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
             for (uint32_t d : {64u, 128u, 256u, 512u}) {
                 for (auto& x : ss) { x.mapping = bm; x.tile = bt; x.delta = d; }
                 std::vector<DevBuf<uint32_t>> hold;
-                const Outcome o = launch_batch(one, ss, false, 2, P->timeout_ms, s.s, nullptr, &hold);
+                const Outcome o = launch_batch(one, ss, false, 2, P->timeout_ms, s.s, nullptr, &hold, group);
                 if (o.ms < bestd) { bestd = o.ms; bd = d; }
             }
         }
@@ -834,7 +1184,8 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
     }
     std::vector<uint32_t*> dist(nq);
     std::vector<DevBuf<uint32_t>> hold;
-    const Outcome o = launch_batch(graphs, qs, P->use_graph != 0, P->replays, P->timeout_ms, s.s, &dist, &hold);
+    const Outcome o = launch_batch(graphs, qs, P->use_graph != 0, P->replays, P->timeout_ms, s.s, &dist, &hold,
+                                   group);
     if (out_mem == SERAPH_MEM_HOST)
         for (uint32_t q = 0; q < nq; ++q)
             SR_CUDA(cudaMemcpyAsync(qin[q].out, dist[q], graphs[qin[q].graph]->n * sizeof(uint32_t),

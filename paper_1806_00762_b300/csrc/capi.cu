@@ -475,6 +475,7 @@ int seraph_batch_params_default(seraph_batch_params* p) {
         p->use_graph = 1;
         p->replays = 1;
         p->timeout_ms = 60000;
+        p->group = 1;
         return SERAPH_OK;
     });
 }

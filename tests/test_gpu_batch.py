@@ -108,3 +108,41 @@ def test_batch_invalid_arguments(work):
         seraph.batch_run(graphs, [(0, "cc", 0)])
     with pytest.raises(SeraphError, match="EINVAL"):
         seraph.batch_run(graphs, [(len(graphs), "bfs", 0)])
+
+
+@pytest.mark.parametrize("group", [0, 1])
+@pytest.mark.parametrize("kw", [dict(mapping="cta", tile=64), dict(mapping="thread", tile=32),
+                                dict(mapping="cta", tile=512, delta=1),
+                                dict(mapping="cta", tile=128, bfs_pull_div=0xFFFFFFFF)],
+                         ids=lambda k: "-".join(f"{a}{b}" for a, b in k.items()))
+def test_grouped_and_single_records_agree_with_the_oracle(work, group, kw):
+    """Queries of one graph and algorithm run as lockstep groups (group = 1:
+    one frontier for the group, interleaved distances, a shared near-far
+    split; BFS groups pulling bottom-up too) or one record each (group = 0):
+    exact either way."""
+    graphs, queries, refs = work
+    outs, st = seraph.batch_run(graphs, queries, group=group, **kw)
+    for o, r in zip(outs, refs):
+        assert np.array_equal(o, r)
+
+
+def test_groups_of_eight_with_duplicate_sources_and_a_remainder(work):
+    """17 SSSP and 11 BFS queries on one graph: groups of 8 and remainders of
+    1 and 3, several queries sharing a source (one frontier entry for all of
+    them), in one launch with queries of other graphs."""
+    graphs, _, _ = work
+    g = 5
+    n = graphs[g].n
+    spec = synth.batch_workload(n_graphs=6, n_queries=48, min_scale=9, max_scale=13)[0][g]
+    src, dst = synth.rmat_edges(spec["scale"], spec["edge_factor"], spec["abcd"], spec["seed"])
+    w = synth.weights(src, dst)
+    og = oracle.build_csr(n, src, dst, w)
+    s = synth.pick_sources(n, synth.has_out_edge(n, src, dst), 12, seed=55)
+    qs = [(g, "sssp", x) for x in s + s[:5]] + [(g, "bfs", x) for x in s[:8] + [s[0]] * 3]
+    qs += [(0, "bfs", 0), (1, "sssp", 3)]
+    outs, _ = seraph.batch_run(graphs, qs, mapping="cta", tile=64)
+    for (gi, algo, x), o in zip(qs[:-2], outs):
+        ref = oracle.sssp(og, x) if algo == "sssp" else oracle.bfs(og, x)
+        assert np.array_equal(o, ref), (algo, x)
+    single, _ = seraph.batch_run(graphs, qs[-2:], mapping="cta", tile=64, group=0)
+    assert np.array_equal(outs[-2], single[0]) and np.array_equal(outs[-1], single[1])
