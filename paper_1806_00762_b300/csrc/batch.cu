@@ -221,15 +221,18 @@ __device__ __forceinline__ uint32_t tag_bits(uint32_t w, uint32_t tag) {
 // with act_j false carry nothing (but still take part in the ballots).
 // Block-aggregated append (all threads of the block call): one atomic per
 // block for the near and far pushes of all its warps.
+// Slot j of a lane goes to the near frontier when pn[j] == kPushNear and to
+// the far pile when pf[j] == kPushFar (a group's edge may do both).
 __device__ __forceinline__ void append_block(BQuery* qs, uint32_t q, const BQuery& Q,
-                                             const int push[kEdgeIlp], const uint32_t v[kEdgeIlp]) {
+                                             const int pn[kEdgeIlp], const int pf[kEdgeIlp],
+                                             const uint32_t v[kEdgeIlp]) {
     __shared__ unsigned s_cnt[2][kNT / 32], s_base[2];
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     unsigned mn[kEdgeIlp], mf[kEdgeIlp], tn = 0, tf = 0;
 #pragma unroll
     for (int j = 0; j < kEdgeIlp; ++j) {
-        mn[j] = __ballot_sync(kFull, push[j] == kPushNear);
-        mf[j] = __ballot_sync(kFull, push[j] == kPushFar);
+        mn[j] = __ballot_sync(kFull, pn[j] == kPushNear);
+        mf[j] = __ballot_sync(kFull, pf[j] == kPushFar);
         tn += __popc(mn[j]);
         tf += __popc(mf[j]);
     }
@@ -247,8 +250,8 @@ __device__ __forceinline__ void append_block(BQuery* qs, uint32_t q, const BQuer
     uint32_t* far = Q.far[Q.fsel];
 #pragma unroll
     for (int j = 0; j < kEdgeIlp; ++j) {
-        if (push[j] == kPushNear) near[bn + __popc(mn[j] & lanemask_lt())] = v[j];
-        if (push[j] == kPushFar) far[bf + __popc(mf[j] & lanemask_lt())] = v[j];
+        if (pn[j] == kPushNear) near[bn + __popc(mn[j] & lanemask_lt())] = v[j];
+        if (pf[j] == kPushFar) far[bf + __popc(mf[j] & lanemask_lt())] = v[j];
         bn += __popc(mn[j]);
         bf += __popc(mf[j]);
     }
@@ -274,7 +277,7 @@ __device__ __forceinline__ void relax_edges(BQuery* qs, uint32_t q, const BQuery
 #pragma unroll
     for (int j = 0; j < kEdgeIlp; ++j) push[j] = ok[j] ? relax(Q, v[j], c[j], seen[j]) : kPushNone;
     if (BLOCK) {
-        append_block(qs, q, Q, push, v);
+        append_block(qs, q, Q, push, push, v);
         return;
     }
     append_many(Q.front[(Q.round + 1) & 1], &qs[q].next_n, push, kPushNear, v);
@@ -451,8 +454,7 @@ __device__ unsigned long long group_near_tile(const BGraphDev& G, BQuery* qs, ui
                 if (far && tag_or(fw + v, Q.epoch + 1, far)) pf[j] = kPushFar;
             }
         }
-        append_block(qs, q, Q, pn, vv);
-        append_block(qs, q, Q, pf, vv);
+        append_block(qs, q, Q, pn, pf, vv);
     }
     __syncthreads();
     return threadIdx.x == 0 ? hi - lo : 0;
