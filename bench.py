@@ -177,7 +177,7 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True,
 # sweeps) -- weighted by the step's 154 PageRank and 64 SSSP relax launches
 # (profiles/relax_kernel_dram_rmat28.md); valid only for the kernel source and
 # the two schedules it was taken on.
-RELAX_TRAFFIC = {"engine_sha256": "927d5f397eb0d637", "bytes_per_launch": 6.4188e9,
+RELAX_TRAFFIC = {"engine_sha256": "645a9233eb068c58", "bytes_per_launch": 6.4323e9,
                  "sssp": DEFAULT_SSSP,
                  "pagerank": DEFAULT_PAGERANK,
                  "workload": "rmat28 default step"}
