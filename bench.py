@@ -415,7 +415,9 @@ def main_batch(args, world, rank):
                          "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                          "algorithmic_bytes_per_step": alg_bytes},
             "edges_processed_per_raw": st["edges"] / raw_edges,
-            "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
+            # per replay: distances init, round-0 init, the persistent kernel and
+            # the scatter of grouped queries' distances
+            "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
