@@ -626,11 +626,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             SR_CUDA(cudaMemcpyAsync(sb, (ch.packed ? g->h_pack.p : g->h_struct.p) + ch.s_begin,
                                     ch.s_bytes, cudaMemcpyHostToDevice, xs.s));
         }
+        // (copy_ms counts the copies on the copy stream: a decoded chunk's
+        // weights, copied after its decode, are not in it)
+        if (prof && ch.decode) SR_CUDA(cudaEventRecord(pc_e[(load_seq + 1) % ring].e, xs.s));
         // weights after the decode (they may overlap the packed staging bytes)
         if (use_w && ch.w_bytes)
             SR_CUDA(cudaMemcpyAsync(sb + ch.w_slot_off, g->h_weight.p + ch.w_begin, ch.w_bytes,
                                     cudaMemcpyHostToDevice, fin));
-        if (prof) SR_CUDA(cudaEventRecord(pc_e[(load_seq + 1) % ring].e, fin));
+        if (prof && !ch.decode) SR_CUDA(cudaEventRecord(pc_e[(load_seq + 1) % ring].e, fin));
         launch_set_locs(loc.p, g->d_vb.p, ch.first_page, ch.end_page, d_rel_soff.p, d_rel_woff.p,
                         d_offb.p, sb, use_w ? sb : nullptr, ch.packed, rs.p, ++load_seq, fin);
         ++launches;

@@ -62,7 +62,7 @@ def test_bench_pagerank_schedule_streams_packed_and_plain_pages(bench_graph):
     import bench
     scale, g, _ = bench_graph
     budget = int(16 * (1 << 30) * 2.0 ** (scale - 28))
-    kw = bench.parse_sched(bench.DEFAULT_PAGERANK)
+    kw = dict(bench.parse_sched(bench.DEFAULT_PAGERANK), stream_packed=0)  # page forms as stored
     _, hy = seraph.run(g, "pagerank", budget_bytes=budget, max_sweeps=1, **kw)
     _, pk = seraph.run(g, "pagerank", budget_bytes=budget, max_sweeps=1, **dict(kw, columns="packed"))
     _, pl = seraph.run(g, "pagerank", budget_bytes=budget, max_sweeps=1, **dict(kw, columns="plain"))
