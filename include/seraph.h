@@ -314,16 +314,21 @@ typedef struct seraph_params {
                                    bound                                     */
     uint32_t stream_packed;     /* 1 (graphs built with SERAPH_COMPRESS): a
                                    chunk processed in the plain form streams
-                                   in its packed form into the far end of its
-                                   ring slot and is decoded on the device into
-                                   the plain form, page by page (each page's
-                                   plain bytes end before its packed bytes
-                                   start), so the host link carries the packed
-                                   bytes; chunks that cannot be laid out so
-                                   stream plain.  Chunks are cut with one
-                                   packed page of slack.  A transfer encoding
-                                   (not in the paper): results unchanged.
-                                   0 = off                                   */
+                                   compact into the far end of its ring slot
+                                   -- per page a header of two bytes per
+                                   vertex (in-degree, LEB128 code bytes;
+                                   larger counts in an escape list) with the
+                                   offsets of every 256th vertex, then the
+                                   page's gap stream -- and is rebuilt on the
+                                   device into the plain form, page by page
+                                   (each page's plain bytes end before its
+                                   staged bytes start), so the host link
+                                   carries neither offset array nor the
+                                   4-byte columns; chunks that cannot be laid
+                                   out so stream plain.  Chunks are cut with
+                                   one staged page of slack.  A transfer
+                                   encoding (not in the paper): results
+                                   unchanged.  0 = off                       */
 } seraph_params;
 
 #define SERAPH_L2_HOT_AUTO UINT64_MAX

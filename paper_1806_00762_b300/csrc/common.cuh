@@ -193,4 +193,13 @@ __device__ __forceinline__ T block_excl_scan(T x, T* ws, T* total) {
     return r;
 }
 
+// Vertices per checkpoint of a streamed header (one CTA's tile when the page
+// is rebuilt on the device).
+constexpr uint32_t kStreamTile = 256;
+__host__ __device__ inline uint64_t stream_ckpt_bytes(uint64_t nv) {
+    return 16 * ((nv + kStreamTile - 1) / kStreamTile + 1);
+}
+__host__ __device__ inline uint64_t stream_hdr_bytes(uint64_t nv) { return (2 * nv + 15) & ~15ull; }
+__host__ __device__ inline uint64_t stream_esc_bytes(uint64_t nesc) { return (8 * nesc + 15) & ~15ull; }
+
 }  // namespace seraph

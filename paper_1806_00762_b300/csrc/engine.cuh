@@ -125,11 +125,13 @@ void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t 
                      const uint64_t* rel_soff, const uint64_t* rel_woff, const uint64_t* off_bytes,
                      uint8_t* sbase, uint8_t* wbase, bool packed, RunState* rs, uint32_t seq,
                      cudaStream_t s);
-// Decode one packed page (off, boff, LEB128 stream at `in`) into its plain
-// form (off, col with zero padding, s_bytes in all, at `out`); the two regions
-// must not overlap.
-void launch_decode_page(const uint8_t* in, uint8_t* out, uint32_t nv, uint64_t off_bytes,
-                        uint64_t s_bytes, cudaStream_t s);
+// Rebuild one page streamed compact (its streamed header -- checkpoints,
+// per-vertex in-degree and code bytes, nesc escapes -- then its LEB128 gap
+// stream, at `in`, 16-byte aligned) into its plain form (off, col with zero
+// padding, s_bytes in all, at `out`, 16-byte aligned); the two regions must
+// not overlap.
+void launch_decode_page(const uint8_t* in, uint8_t* out, uint32_t nv, uint32_t nesc,
+                        uint64_t off_bytes, uint64_t s_bytes, cudaStream_t s);
 void launch_init_values(int algo, const AlgoArgs& a, uint64_t n, uint32_t source,
                         const uint32_t* label0, cudaStream_t s);
 // out[v] = in[inv[v]]: values of a reordered graph back in the caller's ids.

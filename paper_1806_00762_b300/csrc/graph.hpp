@@ -50,7 +50,20 @@ struct PageMeta {
     uint64_t pk_off;    // byte offset of the page in the packed region
     uint64_t pk_bytes;  // packed structure bytes (padded)
     uint64_t pk_data;   // gap-stream bytes (unpadded)
+    // Streamed header of the packed page (SERAPH_COMPRESS), in its own region,
+    // sent ahead of the page's gap stream when a plain page streams compact:
+    //   uint4 ckpt[T+1], T = ceil(nv / kStreamTile): (off, boff, escapes
+    //     before) at vertex t * kStreamTile, and (ne, gap-stream bytes, nesc);
+    //   u16 hdr[nv]: in-degree | code bytes << 8 when both are at most 254,
+    //     else 0xFFFF and the two counts are the vertex's escape entry;
+    //   uint2 esc[nesc]: (in-degree, code bytes) of the escaped vertices in
+    //     vertex order;
+    // hdr and esc each padded to 16 B.
+    uint64_t sh_off;    // byte offset of the header in the header region
+    uint64_t sh_bytes;  // header bytes (multiple of 16)
+    uint32_t sh_nesc;   // escaped vertices
 };
+
 
 struct seraph_graph {
     int device = 0;
@@ -68,6 +81,7 @@ struct seraph_graph {
     seraph::DevBuf<uint32_t> d_zero_in; // bit v set: v has no in-edge
     bool packed = false;               // built with SERAPH_COMPRESS
     seraph::PinnedBuf h_pack;          // all packed page structures, in page order
+    seraph::PinnedBuf h_shdr;          // streamed headers of the packed pages, in page order
     seraph::DevBuf<uint8_t> d_pack_tmp; // gap streams while the graph is built
     RunWorkspace ws;                   // buffers kept between runs
     bool reordered = false;            // built with SERAPH_REORDER

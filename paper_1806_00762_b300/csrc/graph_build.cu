@@ -11,7 +11,9 @@
 //   6. page-relative u32 offsets staged on the device, then every page's
 //      offsets / sources / weights copied into the pinned page images.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -794,6 +796,79 @@ void build_out_edges(seraph_graph* g, uint64_t n, uint64_t E, DevBuf<uint32_t>& 
     g->out_edges = true;
 }
 
+// Runs f(p) for every page p on a few host threads (pages taken in turn).
+template <class F>
+void for_pages(uint32_t P, F f) {
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::atomic<uint32_t> next{0};
+    auto work = [&] {
+        for (uint32_t p; (p = next.fetch_add(1)) < P;) f(p);
+    };
+    std::vector<std::thread> ts;
+    for (unsigned i = 1; i < hw; ++i) ts.emplace_back(work);
+    work();
+    for (auto& t : ts) t.join();
+}
+
+// The header that a packed page streams with when a plain chunk is sent in
+// compact form (PageMeta::sh_*): per vertex two bytes (in-degree, code
+// bytes) instead of the two u32 offsets, plus the offsets of every
+// kStreamTile-th vertex, so the device rebuilds both offset arrays one tile
+// per CTA without a page-wide scan.  Read from the packed pages' own off and
+// boff arrays, on the host.
+static void build_stream_headers(seraph_graph* g) {
+    const uint32_t P = g->num_pages;
+    auto arrays = [&](const PageMeta& pm, const uint32_t*& off, const uint32_t*& boff) {
+        off = (const uint32_t*)(g->h_pack.p + pm.pk_off);
+        boff = (const uint32_t*)(g->h_pack.p + pm.pk_off + pm.off_bytes);
+    };
+    auto escaped = [](uint32_t d, uint32_t l) { return d >= 255u || l >= 255u; };
+    for_pages(P, [&](uint32_t p) {
+        PageMeta& pm = g->pages[p];
+        const uint32_t *off, *boff;
+        arrays(pm, off, boff);
+        uint32_t nesc = 0;
+        for (uint64_t v = 0; v < pm.nv; ++v) nesc += escaped(off[v + 1] - off[v], boff[v + 1] - boff[v]);
+        pm.sh_nesc = nesc;
+        pm.sh_bytes = stream_ckpt_bytes(pm.nv) + stream_hdr_bytes(pm.nv) + stream_esc_bytes(nesc);
+    });
+    uint64_t total = 0;
+    for (uint32_t p = 0; p < P; ++p) {
+        g->pages[p].sh_off = total;
+        total += g->pages[p].sh_bytes;
+    }
+    g->h_shdr.alloc(total);
+    for_pages(P, [&](uint32_t p) {
+        const PageMeta& pm = g->pages[p];
+        const uint32_t *off, *boff;
+        arrays(pm, off, boff);
+        uint8_t* h = g->h_shdr.p + pm.sh_off;
+        std::memset(h, 0, pm.sh_bytes);
+        uint32_t* ck = (uint32_t*)h;
+        uint16_t* hd = (uint16_t*)(h + stream_ckpt_bytes(pm.nv));
+        uint32_t* es = (uint32_t*)(h + stream_ckpt_bytes(pm.nv) + stream_hdr_bytes(pm.nv));
+        uint32_t ne = 0;
+        for (uint64_t v = 0; v <= pm.nv; ++v) {
+            if (v % kStreamTile == 0 || v == pm.nv) {
+                const uint64_t t = (v + kStreamTile - 1) / kStreamTile;  // v / tile, or T at the end
+                ck[4 * t] = off[v];
+                ck[4 * t + 1] = boff[v];
+                ck[4 * t + 2] = ne;
+            }
+            if (v == pm.nv) break;
+            const uint32_t d = off[v + 1] - off[v], l = boff[v + 1] - boff[v];
+            if (escaped(d, l)) {
+                hd[v] = 0xFFFFu;
+                es[2 * ne] = d;
+                es[2 * ne + 1] = l;
+                ++ne;
+            } else {
+                hd[v] = (uint16_t)(d | (l << 8));
+            }
+        }
+    });
+}
+
 // The packed page form (SERAPH_COMPRESS): LEB128 gap streams of every
 // destination's sources, encoded on the device, then laid out per page in
 // pinned memory as off (copied from `stage`), boff and the stream bytes.
@@ -867,6 +942,7 @@ void build_packed(seraph_graph* g, uint64_t n, uint64_t E, const uint32_t* col,
     }
     SR_CUDA(cudaStreamSynchronize(s));
     g->d_pack_tmp.release();
+    build_stream_headers(g);
     g->packed = true;
 }
 

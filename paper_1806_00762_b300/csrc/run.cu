@@ -44,11 +44,16 @@ struct Chunk {
     uint64_t w_slot_off;        // weights start this far into the slot
     uint32_t v_begin, v_end;
     bool packed;                // pages in the packed form (else plain)
-    // stream_packed: the plain chunk streams its packed bytes [pk_begin,
-    // pk_begin + pk_bytes) to slot offset stage_off and is decoded in place
+    // stream_packed: the plain chunk streams compact -- each page's streamed
+    // header and gap stream, pk_bytes in all -- to slot offset stage_off and
+    // is rebuilt in place
     bool decode;
-    uint64_t pk_begin, pk_bytes, stage_off;
+    uint64_t pk_bytes, stage_off;
 };
+
+// Bytes a page stages in its slot when its chunk streams compact: its
+// streamed header, then its gap stream padded to 16 bytes.
+uint64_t staged_bytes(const PageMeta& pm) { return pm.sh_bytes + align_up(pm.pk_data, 16); }
 
 struct Event {
     cudaEvent_t e = nullptr;
@@ -252,7 +257,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             const uint64_t wb = use_w ? pm.w_bytes : 0;
             // a plain page that may stream packed leaves room for its packed
             // form behind the chunk's plain bytes (the decode's staging)
-            const uint64_t slack = stream_packed && !pk ? align_up(pm.pk_bytes, 256) : 0;
+            const uint64_t slack = stream_packed && !pk ? align_up(staged_bytes(pm), 256) : 0;
             if (align_up(sb, 256) + wb > slot_bytes) {
                 SR_CHECK(!strict, SERAPH_EBUDGET,
                          "page " + std::to_string(p) + " (" + std::to_string(sb + wb) +
@@ -269,7 +274,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             }
             if (open) out.push_back(cur);
             cur = Chunk{p, p + 1, pk ? pm.pk_off : pm.s_off, sb, pm.w_off, wb, 0, (uint32_t)pm.vb,
-                        (uint32_t)(pm.vb + pm.nv), pk, false, 0, 0, 0};
+                        (uint32_t)(pm.vb + pm.nv), pk, false, 0, 0};
             open = true;
         }
         if (open) out.push_back(cur);
@@ -292,21 +297,23 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     make_chunks(npk, chunks, true);
     const bool packed = npk > 0;  // some pages stream packed
     for (auto& c : chunks) c.w_slot_off = align_up(c.s_bytes, 256);
-    // Streaming a plain chunk packed: its packed pages go to the far end of
-    // the slot and page j is decoded into its plain place, which must end
-    // before page j's packed bytes start (pages are decoded in order, so an
-    // earlier page's packed bytes may be overwritten once decoded).
+    // Streaming a plain chunk compact: its pages' streamed headers and gap
+    // streams go to the far end of the slot and page j is rebuilt into its
+    // plain place, which must end before page j's staged bytes start (pages
+    // are rebuilt in order, so an earlier page's staged bytes may be
+    // overwritten once used).
     for (auto& c : chunks) {
         if (!stream_packed || c.packed) continue;
-        c.pk_begin = g->pages[c.first_page].pk_off;
-        const PageMeta& last = g->pages[c.end_page - 1];
-        c.pk_bytes = last.pk_off + last.pk_bytes - c.pk_begin;
+        c.pk_bytes = 0;
+        for (uint32_t p = c.first_page; p < c.end_page; ++p) c.pk_bytes += staged_bytes(g->pages[p]);
         if (c.pk_bytes >= c.s_bytes || c.pk_bytes > slot_bytes) continue;
         c.stage_off = (slot_bytes - c.pk_bytes) & ~255ull;
         bool fits = true;
+        uint64_t rel = 0;
         for (uint32_t p = c.first_page; p < c.end_page && fits; ++p) {
             const PageMeta& pm = g->pages[p];
-            fits = (pm.s_off - c.s_begin) + pm.s_bytes <= c.stage_off + (pm.pk_off - c.pk_begin);
+            fits = (pm.s_off - c.s_begin) + pm.s_bytes <= c.stage_off + rel;
+            rel += staged_bytes(pm);
         }
         c.decode = fits;
     }
@@ -607,19 +614,30 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         if (prof) SR_CUDA(cudaEventRecord(pc_b[(load_seq + 1) % ring].e, xs.s));
         cudaStream_t fin = xs.s;  // the stream that finishes the load
         if (ch.decode) {
-            // packed bytes to the far end of the slot, then (on the decode
-            // stream, so the copy engine moves on to the next chunk) each page
-            // decoded into its plain place, in page order
-            SR_CUDA(cudaMemcpyAsync(sb + ch.stage_off, g->h_pack.p + ch.pk_begin, ch.pk_bytes,
-                                    cudaMemcpyHostToDevice, xs.s));
+            // each page's streamed header and gap stream to the far end of
+            // the slot, then (on the decode stream, so the copy engine moves
+            // on to the next chunk) each page rebuilt in its plain place, in
+            // page order
+            uint64_t rel = 0;
+            for (uint32_t p = ch.first_page; p < ch.end_page; ++p) {
+                const PageMeta& pm = g->pages[p];
+                uint8_t* dst = sb + ch.stage_off + rel;
+                SR_CUDA(cudaMemcpyAsync(dst, g->h_shdr.p + pm.sh_off, pm.sh_bytes,
+                                        cudaMemcpyHostToDevice, xs.s));
+                if (pm.pk_data)
+                    SR_CUDA(cudaMemcpyAsync(dst + pm.sh_bytes, g->h_pack.p + pm.pk_off + 2 * pm.off_bytes,
+                                            align_up(pm.pk_data, 16), cudaMemcpyHostToDevice, xs.s));
+                rel += staged_bytes(pm);
+            }
             SR_CUDA(cudaEventRecord(staged[c].e, xs.s));
             SR_CUDA(cudaStreamWaitEvent(ds.s, staged[c].e, 0));
             fin = ds.s;
+            rel = 0;
             for (uint32_t p = ch.first_page; p < ch.end_page; ++p) {
                 const PageMeta& pm = g->pages[p];
-                launch_decode_page(sb + ch.stage_off + (pm.pk_off - ch.pk_begin),
-                                   sb + (pm.s_off - ch.s_begin), (uint32_t)pm.nv, pm.off_bytes,
-                                   pm.s_bytes, ds.s);
+                launch_decode_page(sb + ch.stage_off + rel, sb + (pm.s_off - ch.s_begin),
+                                   (uint32_t)pm.nv, pm.sh_nesc, pm.off_bytes, pm.s_bytes, ds.s);
+                rel += staged_bytes(pm);
                 ++launches;
             }
         } else {

@@ -57,8 +57,9 @@ def test_failed_pinned_allocation_in_graph_build_returns_enomem_and_keeps_nothin
     # one full build first, so lazily created driver state is not counted
     seraph.Graph.from_edges(n, src, dst, w, num_pages=8, compress=True).free()
     pinned0, free0 = seraph.debug_pinned_bytes(), _free_device_bytes()
-    # the build pins page structures, weights and packed pages: fail each
-    for k in (1, 2, 3):
+    # the build pins page structures, weights, packed pages and the packed
+    # pages' streamed headers: fail each
+    for k in (1, 2, 3, 4):
         seraph.debug_fail_pinned_alloc(k)
         try:
             with pytest.raises(seraph.SeraphError) as ei:

@@ -1,16 +1,19 @@
-"""Plain chunks streamed in their packed form and decoded on the device
-(seraph_params.stream_packed): the host link carries the LEB128 pages, a
-decode kernel rebuilds each page's plain form in the ring slot (page by
-page, each page's plain bytes ending before its packed bytes start), and the
+"""Plain chunks streamed compact and rebuilt on the device
+(seraph_params.stream_packed): the host link carries, per page, a header of
+two bytes per vertex (in-degree, code bytes; larger counts escaped) with a
+checkpoint of both offsets every 256 vertices, and the page's LEB128 gap
+stream; a kernel rebuilds each page's plain form in the ring slot (page by
+page, each page's plain bytes ending before its staged bytes start), and the
 run relaxes plain pages as before.
 
 Checked against the oracle -- bit-exact for SSSP, BFS and CC, within the
 PageRank tolerance -- for plain and hybrid page forms, resident and
 streamed rings (every sweep decodes again), windows 1 and 4, vertex
 orders, weight widths of 1, 2 and 4 bytes, hub vertices whose code bytes
-need the warp decode, and graphs of a few vertices; fewer bytes streamed
-than without it; a ring too small for the staging falls back to plain
-copies; a graph without the packed form is rejected."""
+need the warp decode, escaped counts at and around tile boundaries of
+ragged pages, and graphs of a few vertices; fewer bytes streamed than
+without it; a ring too small for the staging falls back to plain copies; a
+graph without the packed form is rejected."""
 import numpy as np
 import pytest
 
@@ -121,6 +124,38 @@ def test_stream_packed_hubs_and_tiny_graphs():
             ref = oracle.sssp(og, 1) if algo == "sssp" else oracle.bfs(og, 1)
             assert np.array_equal(got, ref), (n, algo)
         g.free()
+
+
+def test_stream_compact_escapes_at_tile_boundaries():
+    """In-degrees and code byte counts on both sides of the one-byte limit
+    (254, 255, 256 and beyond; long codes push the byte count over it at
+    in-degrees below 255), placed on the vertices around each 256-vertex
+    checkpoint of pages whose last tile is partial."""
+    rng = np.random.default_rng(7)
+    n = 40000  # gaps of ~200 between a vertex's sources: mostly 2-byte codes
+    deg = np.zeros(n, np.int64)
+    for b in range(0, n, 256):
+        for off, d in ((-2, 254), (-1, 255), (0, 256), (1, 600), (2, 0), (3, 1), (5, 200)):
+            if 0 <= b + off < n:
+                deg[b + off] = d
+    rest = deg == 0
+    deg[rest] = rng.integers(0, 4, rest.sum())
+    dst = np.repeat(np.arange(n, dtype=np.int64), deg)
+    src = np.concatenate([rng.choice(n, d, replace=False) for d in deg if d > 0])
+    keep = src != dst
+    src, dst = src[keep].astype(np.uint32), dst[keep].astype(np.uint32)
+    w = (rng.integers(1, 256, len(src))).astype(np.uint32)
+    og = oracle_graph(n, src, dst, w)
+    # in-degrees 200 and 254 (no escape by in-degree) take more than 254 code bytes
+    g = seraph.Graph.from_edges(n, src, dst, w, num_pages=3, compress=True)
+    for algo in ("sssp", "bfs"):
+        for src_v in (0, 1, 30001):
+            got, st = seraph.run(g, algo, source=src_v, window=1, slots=2, columns="plain",
+                                 stream_packed=1, budget_bytes=plain_budget(g, 2, algo == "sssp", 1.2))
+            assert st["resident"] == 0
+            ref = oracle.sssp(og, src_v) if algo == "sssp" else oracle.bfs(og, src_v)
+            assert np.array_equal(got, ref), (algo, src_v)
+    g.free()
 
 
 def test_stream_packed_falls_back_without_room_and_needs_packed_pages(r14):
