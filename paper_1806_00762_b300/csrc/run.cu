@@ -285,9 +285,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     if (hybrid) {
         // the fewest packed pages (the first pages hold the most-connected
         // destinations when vertices are in out-degree order, and their gaps
-        // are short) with which every chunk stays resident in the ring
+        // are short) with which every chunk stays resident in the ring; never
+        // a page from the first one whose packed form is not smaller than its
+        // plain form on (the tail of many vertices with few in-edges), so a
+        // ring that cannot hold the graph packs exactly the pages that shrink
+        uint32_t shrink = 0;
+        while (shrink < g->num_pages && g->pages[shrink].pk_bytes < g->pages[shrink].s_bytes) ++shrink;
         std::vector<Chunk> trial;
-        uint32_t lo = 0, hi = g->num_pages;
+        uint32_t lo = 0, hi = make_chunks(shrink, trial, false) ? shrink : g->num_pages;
         while (lo < hi) {  // (a split whose plain pages do not fit a slot counts as too few)
             const uint32_t mid = (lo + hi) / 2;
             if (make_chunks(mid, trial, false) && trial.size() <= R) hi = mid; else lo = mid + 1;
