@@ -175,23 +175,25 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True,
 # the default step at full size -- three PageRank launches (plain columns, the
 # resident sweeps) and three SSSP launches (packed columns, the resident
 # sweeps) -- weighted by the step's 154 PageRank and 64 SSSP relax launches
-# (profiles/relax_kernel_dram_rmat28.md); valid only for the kernel source and
-# the two schedules it was taken on.
-RELAX_TRAFFIC = {"engine_sha256": "645a9233eb068c58", "bytes_per_launch": 6.4323e9,
+# (profiles/relax_kernel_dram_rmat28.md); valid only for the kernel sources
+# (engine.cu and leb128.cuh) and the two schedules it was taken on.
+RELAX_TRAFFIC = {"kernel_sha256": "2c17ecc59c18a7bb", "bytes_per_launch": 6.4342e9,
                  "sssp": DEFAULT_SSSP,
                  "pagerank": DEFAULT_PAGERANK,
                  "workload": "rmat28 default step"}
+RELAX_SOURCES = ("engine.cu", "leb128.cuh")
 
 
 def relax_traffic(args) -> float | None:
     import hashlib
-    src = os.path.join(ROOT, "paper_1806_00762_b300", "csrc", "engine.cu")
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in RELAX_SOURCES:
+        with open(os.path.join(ROOT, "paper_1806_00762_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
     default = (args.scale == 28 and args.pages == 512 and args.budget_gb == 16.0 and
                args.vertex_order == "degree" and args.sssp == RELAX_TRAFFIC["sssp"] and
                args.pagerank == RELAX_TRAFFIC["pagerank"] and args.algos == "sssp,pagerank")
-    if sha != RELAX_TRAFFIC["engine_sha256"] or not default:
+    if h.hexdigest()[:16] != RELAX_TRAFFIC["kernel_sha256"] or not default:
         return None
     return RELAX_TRAFFIC["bytes_per_launch"]
 

@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "engine.cuh"
+#include "leb128.cuh"
 
 namespace seraph {
 namespace {
@@ -27,51 +28,6 @@ namespace {
 constexpr int kNT = 256;
 constexpr int kCompactRounds = 4;
 constexpr uint32_t kCompactTile = kNT * kCompactRounds;
-
-// L2 eviction-priority policies (createpolicy, sm_80+).  Page data of the
-// resident chunk is read once per pass (evict-first); the gathered values of
-// the lowest-numbered `hot` vertices -- the most-read ones once vertices are
-// numbered by out-degree -- are kept (evict-last).
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_normal() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-// Streaming loads of the resident chunk (read-only while a pass runs; not
-// kept in L1).  Not volatile: the compiler may batch them for more loads in
-// flight.
-__device__ __forceinline__ uint4 ld_stream4(const void* p, uint64_t pol) {
-    uint4 r;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p), "l"(pol));
-    return r;
-}
-
-__device__ __forceinline__ uint2 ld_stream2(const void* p, uint64_t pol) {
-    uint2 r;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
-        : "=r"(r.x), "=r"(r.y)
-        : "l"(p), "l"(pol));
-    return r;
-}
-
-__device__ __forceinline__ uint32_t ld_stream(const void* p, uint64_t pol) {
-    uint32_t r;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
-    return r;
-}
 
 // Gathered source value (weak load: values may change during a pass).
 __device__ __forceinline__ uint32_t ld_gather(const void* p, uint64_t pol) {
@@ -276,33 +232,6 @@ __device__ __forceinline__ void gather8(const AlgoArgs& a, const PageLoc& loc, u
     }
 }
 
-// ----------------------------------------------------------- packed pages
-// A destination's sources are its first id, then each gap to the next id
-// minus one, as LEB128 codes (SERAPH_COMPRESS).  Lanes take aligned 16-byte
-// pieces of the code bytes and decode the codes that start in their piece:
-// a byte starts a code when the byte before it ends one (high bit clear).
-// The ids follow from a running sum, across pieces by a scan of the per-piece
-// (count, sum of value + 1) pairs.
-
-// Bit i (0..3) set: byte i of w ends a code.
-__device__ __forceinline__ uint32_t leb_ends4(uint32_t w) {
-    // the four flag bits (7, 15, 23, 31) gathered into bits 28..31 by one
-    // multiply: the other partial products land on distinct bits below 24
-    return ((~w & 0x80808080u) * 0x00204081u) >> 28;
-}
-
-// Bits of the 16 bytes at c that start a code of the range [B, Eb); pt = the
-// byte before c ends a code (or c is the range's first piece).
-__device__ __forceinline__ uint32_t leb_starts(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
-                                               uint32_t pt, uint32_t c, uint32_t B, uint32_t Eb) {
-    const uint32_t T = leb_ends4(w0) | (leb_ends4(w1) << 4) | (leb_ends4(w2) << 8) |
-                       (leb_ends4(w3) << 12);
-    const uint32_t lo = B > c ? B - c : 0u;                  // < 16
-    const uint32_t hi = Eb - c < 16u ? Eb - c : 16u;         // c < Eb
-    const uint32_t rng = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
-    return ((T << 1) | pt) & rng;
-}
-
 template <int WB>
 __device__ __forceinline__ uint32_t ld_weight1(const uint8_t* w, uint32_t idx, uint64_t pol) {
     uint32_t r;
@@ -313,54 +242,6 @@ __device__ __forceinline__ uint32_t ld_weight1(const uint8_t* w, uint32_t idx, u
     else
         asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(w + 4 * (uint64_t)idx), "l"(pol));
     return r;
-}
-
-// One aligned 16-byte piece of a code range: the piece, the 4 bytes after it
-// (when still inside the range) and whether the byte before it ends a code.
-struct Piece {
-    uint32_t w0, w1, w2, w3, w4, pt;
-};
-
-// The 7-bit groups of 4 code bytes packed into 28 bits.
-__device__ __forceinline__ uint32_t leb_payload4(uint32_t w) {
-    const uint32_t t = (w & 0x007F007Fu) | ((w & 0x7F007F00u) >> 1);  // byte pairs -> 14 bits
-    return (t & 0x3FFFu) | ((t >> 2) & 0xFFFC000u);
-}
-
-// Every code start of a piece decoded at once.  The 7-bit groups of the 20
-// window bytes are packed into one bit stream (byte j's group at bit 7j) and
-// their end flags into a second one (a code's last byte flags bit 7j + 6), so
-// the code starting at byte j is x & (e ^ (e - 1)) with x, e the 32 bits of
-// the two streams from bit 7j: the mask keeps everything up to the first end
-// flag (all 32 bits for a 5-byte code, whose value fits them exactly).  The
-// byte positions are compile-time constants once unrolled.  lid[j] = sum of
-// (value + 1) over the codes starting at or before byte j, i.e. the id of the
-// code at j relative to the id before the piece.  Returns the piece's total.
-__device__ __forceinline__ uint32_t piece_decode(const Piece& P, uint32_t st, uint32_t lid[16]) {
-    const uint32_t w[5] = {P.w0, P.w1, P.w2, P.w3, P.w4};
-    uint32_t p[5], q[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        p[k] = leb_payload4(w[k]);
-        // end flags of the 4 bytes spread to bits 6, 13, 20, 27 (the product
-        // terms of distinct bits land on distinct bits: no carries)
-        q[k] = (leb_ends4(w[k]) * 0x01041040u) & 0x08102040u;
-    }
-    const uint32_t sw[6] = {p[0] | (p[1] << 28), (p[1] >> 4) | (p[2] << 24), (p[2] >> 8) | (p[3] << 20),
-                            (p[3] >> 12) | (p[4] << 16), p[4] >> 16, 0u};
-    const uint32_t se[6] = {q[0] | (q[1] << 28), (q[1] >> 4) | (q[2] << 24), (q[2] >> 8) | (q[3] << 20),
-                            (q[3] >> 12) | (q[4] << 16), q[4] >> 16, 0u};
-    uint32_t acc = 0;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int o = 7 * j;
-        const uint32_t x = __funnelshift_r(sw[o >> 5], sw[(o >> 5) + 1], o & 31);
-        const uint32_t e = __funnelshift_r(se[o >> 5], se[(o >> 5) + 1], o & 31);
-        const uint32_t v = x & (e ^ (e - 1u));
-        acc += ((st >> j) & 1u) ? v + 1u : 0u;
-        lid[j] = acc;
-    }
-    return acc;
 }
 
 // Gathers and reduction of a decoded piece, eight codes in flight at a time,
@@ -415,16 +296,6 @@ __device__ __forceinline__ void piece_gather(const AlgoArgs& a, const PageLoc& l
             }
         }
     }
-}
-
-__device__ __forceinline__ Piece load_piece(const uint8_t* d, uint32_t c, uint32_t A, uint32_t Eb,
-                                            uint64_t pol) {
-    Piece P;
-    const uint4 q = ld_stream4(d + c, pol);
-    P.w0 = q.x; P.w1 = q.y; P.w2 = q.z; P.w3 = q.w;
-    P.w4 = c + 16u < Eb ? ld_stream(d + c + 16u, pol) : 0u;
-    P.pt = c == A ? 1u : ((ld_stream(d + c - 4u, pol) >> 31) ^ 1u);
-    return P;
 }
 
 // Thread per vertex: the pieces one after another, the running id carried.
@@ -521,133 +392,6 @@ __device__ __forceinline__ void edges_packed_cta(const AlgoArgs& a, const PageLo
                                           ord + (uint32_t)(ex >> 32), macc, sacc);
         run += (uint32_t)tot;
         ord += (uint32_t)(tot >> 32);
-    }
-}
-
-// ------------------------------------------------ packed -> plain decode
-// A chunk can stream in its packed form and be decoded on the device into
-// the plain form it is processed in (fewer bytes over the host link).  The
-// ids of a decoded piece are written out instead of gathered: the code at
-// byte j has id run + lid[j] and edge index ord + (codes before j).
-__device__ __forceinline__ void piece_write(uint32_t* col, uint32_t st, const uint32_t lid[16],
-                                            uint32_t run, uint32_t ord, uint32_t ne) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const uint32_t i = ord + __popc(st & ((1u << j) - 1u));
-        if (((st >> j) & 1u) && i < ne) col[i] = run + lid[j];
-    }
-}
-
-// Decodes the code bytes [B, Eb) of each lane's vertex (when `valid`) into
-// col from edge index e0: a vertex of at most 64 code bytes by its own lane,
-// longer ones by the whole warp (pieces t, t+32, ... and a warp scan).
-// Called by whole warps.
-__device__ __forceinline__ void decode_warp(const uint8_t* d, uint32_t* col, uint32_t ne, bool valid,
-                                            uint32_t B, uint32_t Eb, uint32_t e0, uint64_t pol) {
-    const uint32_t lane = lane_id();
-    const bool big = valid && Eb - B > 64u;
-    if (valid && !big) {
-        const uint32_t A = B & ~15u;
-        uint32_t run = 0xFFFFFFFFu, ord = e0;
-        for (uint32_t c = A; c < Eb; c += 16) {
-            const Piece P = load_piece(d, c, A, Eb, pol);
-            const uint32_t st = leb_starts(P.w0, P.w1, P.w2, P.w3, P.pt, c, B, Eb);
-            uint32_t lid[16];
-            const uint32_t sum = piece_decode(P, st, lid);
-            piece_write(col, st, lid, run, ord, ne);
-            run += sum;
-            ord += __popc(st);
-        }
-    }
-    for (unsigned m = __ballot_sync(kFull, big); m; m &= m - 1) {
-        const int j = __ffs(m) - 1;
-        const uint32_t Bj = __shfl_sync(kFull, B, j), Ej = __shfl_sync(kFull, Eb, j);
-        const uint32_t ej = __shfl_sync(kFull, e0, j);
-        const uint32_t A = Bj & ~15u;
-        const uint32_t pieces = (Ej - A + 15u) >> 4;
-        uint32_t run = 0xFFFFFFFFu, ord = ej;
-        for (uint32_t it = 0; it < (pieces + 31) / 32; ++it) {
-            const uint32_t c = A + 16u * (it * 32 + lane);
-            Piece P{0u, 0u, 0u, 0u, 0u, 0u};
-            uint32_t st = 0;
-            if (c < Ej) {
-                P = load_piece(d, c, A, Ej, pol);
-                st = leb_starts(P.w0, P.w1, P.w2, P.w3, P.pt, c, Bj, Ej);
-            }
-            uint32_t lid[16];
-            const uint64_t x = ((uint64_t)__popc(st) << 32) | piece_decode(P, st, lid);
-            uint64_t inc = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint64_t y = __shfl_up_sync(kFull, inc, o);
-                if (lane >= (uint32_t)o) inc += y;
-            }
-            const uint64_t ex = inc - x;
-            const uint64_t tot = __shfl_sync(kFull, inc, 31);
-            if (st) piece_write(col, st, lid, run + (uint32_t)ex, ord + (uint32_t)(ex >> 32), ne);
-            run += (uint32_t)tot;
-            ord += (uint32_t)(tot >> 32);
-        }
-    }
-}
-
-// One page streamed compact: `in` = its header (checkpoints, per-vertex
-// in-degree and code bytes, escapes; layout in common.cuh) followed by its
-// gap stream; `out` = its plain form (off, col with zero padding, s_bytes in
-// all).  The regions must not overlap.  A CTA takes a tile of kStreamTile
-// vertices, one per thread: the escaped vertices find their entries by a
-// count of the escapes before them, a block scan of (in-degree, code bytes)
-// from the tile's checkpoint gives each vertex's edge and byte offsets, and
-// each warp then decodes its 32 vertices.  Offsets are clamped to the page's
-// totals, so a damaged header cannot move a read or a write off the page.
-__global__ void __launch_bounds__(kNT) decode_page_kernel(const uint8_t* __restrict__ in,
-                                                          uint8_t* __restrict__ out, uint32_t nv,
-                                                          uint32_t nesc, uint64_t off_bytes,
-                                                          uint64_t s_bytes) {
-    static_assert(kStreamTile == kNT, "one vertex per thread");
-    __shared__ unsigned long long ws[kNT / 32 + 1];
-    __shared__ unsigned s_esc[kNT / 32];
-    const uint4* ck = (const uint4*)in;
-    const uint64_t ckb = stream_ckpt_bytes(nv), hb = stream_hdr_bytes(nv);
-    const uint16_t* hdr = (const uint16_t*)(in + ckb);
-    const uint2* esc = (const uint2*)(in + ckb + hb);
-    const uint8_t* d = in + ckb + hb + stream_esc_bytes(nesc);
-    uint32_t* ooff = (uint32_t*)out;
-    uint32_t* col = (uint32_t*)(out + off_bytes);
-    const uint32_t T = (nv + kStreamTile - 1) / kStreamTile;
-    const uint4 last = ck[T];
-    const uint32_t ne = min(last.x, (uint32_t)((s_bytes - off_bytes) / 4)), nb = last.y;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    // the last offset and the zero padding of both arrays (a padding column
-    // may be gathered, so it must be a valid vertex id)
-    for (uint64_t i = (uint64_t)nv + tid; i < off_bytes / 4; i += stride) ooff[i] = i == nv ? ne : 0u;
-    for (uint64_t i = (uint64_t)ne + tid; i < (s_bytes - off_bytes) / 4; i += stride) col[i] = 0u;
-    const uint64_t pol = policy_evict_first();
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
-        const uint4 c0 = ck[t];
-        const uint32_t v = t * kStreamTile + threadIdx.x;
-        const bool valid = v < nv;
-        const uint32_t h = valid ? hdr[v] : 0u;
-        const bool x = h == 0xFFFFu;
-        const unsigned m = __ballot_sync(kFull, x);
-        if (lane == 0) s_esc[warp] = __popc(m);
-        __syncthreads();
-        uint32_t k = c0.z + __popc(m & lanemask_lt());
-        for (uint32_t w = 0; w < warp; ++w) k += s_esc[w];
-        uint32_t deg = h & 0xFFu, len = h >> 8;
-        if (x) {
-            const uint2 e = k < nesc ? esc[k] : make_uint2(0u, 0u);
-            deg = e.x;
-            len = e.y;
-        }
-        unsigned long long tot;
-        const unsigned long long ex =
-            block_excl_scan<kNT>(((unsigned long long)deg << 32) | len, ws, &tot);
-        const uint32_t e0 = min(c0.x + (uint32_t)(ex >> 32), ne);
-        const uint32_t B = min(c0.y + (uint32_t)ex, nb), Eb = min(B + len, nb);
-        if (valid) ooff[v] = e0;
-        decode_warp(d, col, ne, valid, B, Eb, e0, pol);
     }
 }
 
@@ -1351,15 +1095,6 @@ void launch_set_locs(PageLoc* loc, const uint32_t* vb, uint32_t first, uint32_t 
     unsigned g = end > first ? (end - first + kNT - 1) / kNT : 1;
     set_locs_kernel<<<g, kNT, 0, s>>>(loc, vb, first, end, rel_soff, rel_woff, off_bytes, sbase,
                                        wbase, packed, rs, seq);
-    SR_LAUNCH();
-}
-
-void launch_decode_page(const uint8_t* in, uint8_t* out, uint32_t nv, uint32_t nesc,
-                        uint64_t off_bytes, uint64_t s_bytes, cudaStream_t s) {
-    const uint64_t tiles = ((uint64_t)nv + kStreamTile - 1) / kStreamTile;
-    const unsigned g = (unsigned)std::max<uint64_t>(
-        1, std::min<uint64_t>(tiles, (uint64_t)device_sms() * 8));
-    decode_page_kernel<<<g, kNT, 0, s>>>(in, out, nv, nesc, off_bytes, s_bytes);
     SR_LAUNCH();
 }
 

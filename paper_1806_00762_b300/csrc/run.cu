@@ -496,12 +496,15 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     }
 
     // -------------------------------------------------------------- events
-    std::vector<Event> step_done(ring), copy_done(C), staged(C);
+    // staged[p]: page p's compact bytes are in its slot (the rebuild of a
+    // page waits for its own copies, not for the whole chunk's)
+    std::vector<Event> step_done(ring), copy_done(C), staged(g->num_pages);
     std::vector<uint32_t> npass_of(ring, 0);
     for (auto& e : step_done) e.create(false);
     for (auto& e : copy_done) e.create(false);
-    for (uint32_t c = 0; c < C; ++c)
-        if (chunks[c].decode) staged[c].create(false);
+    for (const Chunk& c : chunks)
+        if (c.decode)
+            for (uint32_t p = c.first_page; p < c.end_page; ++p) staged[p].create(false);
     Event ev_start, ev_stop, ev_sweep;
     ev_start.create(true);
     ev_stop.create(true);
@@ -621,8 +624,8 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         if (ch.decode) {
             // each page's streamed header and gap stream to the far end of
             // the slot, then (on the decode stream, so the copy engine moves
-            // on to the next chunk) each page rebuilt in its plain place, in
-            // page order
+            // on) each page rebuilt in its plain place as soon as its own
+            // bytes have landed, in page order
             uint64_t rel = 0;
             for (uint32_t p = ch.first_page; p < ch.end_page; ++p) {
                 const PageMeta& pm = g->pages[p];
@@ -632,19 +635,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
                 if (pm.pk_data)
                     SR_CUDA(cudaMemcpyAsync(dst + pm.sh_bytes, g->h_pack.p + pm.pk_off + 2 * pm.off_bytes,
                                             align_up(pm.pk_data, 16), cudaMemcpyHostToDevice, xs.s));
-                rel += staged_bytes(pm);
-            }
-            SR_CUDA(cudaEventRecord(staged[c].e, xs.s));
-            SR_CUDA(cudaStreamWaitEvent(ds.s, staged[c].e, 0));
-            fin = ds.s;
-            rel = 0;
-            for (uint32_t p = ch.first_page; p < ch.end_page; ++p) {
-                const PageMeta& pm = g->pages[p];
-                launch_decode_page(sb + ch.stage_off + rel, sb + (pm.s_off - ch.s_begin),
-                                   (uint32_t)pm.nv, pm.sh_nesc, pm.off_bytes, pm.s_bytes, ds.s);
+                SR_CUDA(cudaEventRecord(staged[p].e, xs.s));
+                SR_CUDA(cudaStreamWaitEvent(ds.s, staged[p].e, 0));
+                launch_decode_page(dst, sb + (pm.s_off - ch.s_begin), (uint32_t)pm.nv, pm.sh_nesc,
+                                   pm.off_bytes, pm.s_bytes, ds.s);
                 rel += staged_bytes(pm);
                 ++launches;
             }
+            fin = ds.s;
         } else {
             SR_CUDA(cudaMemcpyAsync(sb, (ch.packed ? g->h_pack.p : g->h_struct.p) + ch.s_begin,
                                     ch.s_bytes, cudaMemcpyHostToDevice, xs.s));

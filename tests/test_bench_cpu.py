@@ -56,10 +56,11 @@ def _args(**kw):
 
 
 def test_relax_traffic_only_for_the_captured_source_and_schedules():
-    src = os.path.join(bench.ROOT, "paper_1806_00762_b300", "csrc", "engine.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in bench.RELAX_SOURCES:
+        h.update(open(os.path.join(bench.ROOT, "paper_1806_00762_b300", "csrc", name), "rb").read())
     got = bench.relax_traffic(_args())
-    if sha == bench.RELAX_TRAFFIC["engine_sha256"]:
+    if h.hexdigest()[:16] == bench.RELAX_TRAFFIC["kernel_sha256"]:
         assert got == bench.RELAX_TRAFFIC["bytes_per_launch"]
     else:
         assert got is None
