@@ -276,9 +276,12 @@ typedef struct seraph_params {
                                    evict-last priority and streamed page data
                                    with evict-first, so the most-read values
                                    stay in L2 (pair with SERAPH_REORDER, which
-                                   puts them first); the run raises the
-                                   context's persisting-L2 limit to that size
-                                   and restores it on return.  0 = no hints;
+                                   puts them first); a graph's first such run
+                                   raises the context's persisting-L2 limit to
+                                   that size, and it stays raised until the
+                                   last graph holding it is freed or has its
+                                   buffers released, when the earlier value
+                                   comes back.  0 = no hints;
                                    the default SERAPH_L2_HOT_AUTO = 3/8 of
                                    the device's L2.  Never changes a result. */
     double   pr_omega;          /* PageRank over-relaxation (not in the paper):
@@ -601,9 +604,15 @@ int  seraph_batch_run(seraph_bgraph* const* graphs, uint32_t ng, const seraph_qu
  * seraph_debug_pinned_bytes(): pinned host bytes the library holds right now
  * (all graphs, runs and buffers of the process), so that a test can check
  * that a failed call gave back everything it allocated.
+ * seraph_debug_l2_setaside(bytes): the current context's persisting-L2
+ * set-aside limit (cudaLimitPersistingL2CacheSize) in *bytes.  Runs that keep
+ * their hot range in L2 raise it once per graph and leave it raised until the
+ * graph is freed or its buffers released; then the earlier value comes back.
+ * Returns SERAPH_ECUDA if the limit cannot be read.
  */
 int      seraph_debug_fail_pinned_alloc(uint32_t k);
 uint64_t seraph_debug_pinned_bytes(void);
+int      seraph_debug_l2_setaside(uint64_t* bytes);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* seraph_last_error(void);

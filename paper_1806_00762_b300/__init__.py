@@ -304,6 +304,14 @@ def debug_pinned_bytes() -> int:
     return int(C.lib().seraph_debug_pinned_bytes())
 
 
+def debug_l2_setaside() -> int:
+    """The context's persisting-L2 set-aside limit in bytes
+    (seraph_debug_l2_setaside)."""
+    v = C.u64(0)
+    C.check(C.lib().seraph_debug_l2_setaside(ctypes.byref(v)))
+    return int(v.value)
+
+
 def gather_probe(n_values, n_gathers, hot_values, hot_frac=1.0, reps=5, stream=None) -> float:
     """Fastest of `reps` timed launches (seconds) of the random-gather probe:
     n_gathers 4-byte reads of n_values device values, a fraction hot_frac of

@@ -147,6 +147,7 @@ PROTOTYPES = {
                                         ctypes.POINTER(BatchParams), ctypes.POINTER(BatchStats)]),
     "seraph_debug_fail_pinned_alloc": (ctypes.c_int, [u32]),
     "seraph_debug_pinned_bytes": (u64, []),
+    "seraph_debug_l2_setaside": (ctypes.c_int, [ctypes.POINTER(u64)]),
     "seraph_last_error": (ctypes.c_char_p, []),
     "seraph_version": (ctypes.c_char_p, []),
 }

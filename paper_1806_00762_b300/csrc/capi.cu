@@ -4,6 +4,8 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <vector>
 #include <new>
 #include <string>
@@ -64,6 +66,49 @@ bool take_injected_pinned_failure() {
 }
 
 void note_pinned_bytes(int64_t delta) { g_pinned_bytes += delta; }
+
+namespace {
+std::mutex g_l2_mu;
+std::set<const void*> g_l2_holders;
+bool g_l2_raised = false;
+size_t g_l2_orig = 0, g_l2_now = 0;
+}  // namespace
+
+void l2_setaside_hold(const void* holder, int device, uint64_t bytes) {
+    std::lock_guard<std::mutex> lk(g_l2_mu);
+    int maxp = 0;
+    if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, device) != cudaSuccess ||
+        maxp <= 0) {
+        (void)cudaGetLastError();
+        return;
+    }
+    const size_t want = bytes < (uint64_t)maxp ? (size_t)bytes : (size_t)maxp;
+    if (!g_l2_raised) {
+        if (cudaDeviceGetLimit(&g_l2_orig, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
+        g_l2_now = g_l2_orig;
+    }
+    if (g_l2_now < want) {
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
+        g_l2_now = want;
+        g_l2_raised = true;
+    }
+    if (g_l2_raised) g_l2_holders.insert(holder);
+}
+
+void l2_setaside_drop(const void* holder) {
+    std::lock_guard<std::mutex> lk(g_l2_mu);
+    if (!g_l2_holders.erase(holder) || !g_l2_holders.empty() || !g_l2_raised) return;
+    (void)cudaCtxResetPersistingL2Cache();
+    (void)cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_orig);
+    (void)cudaGetLastError();
+    g_l2_raised = false;
+}
 }  // namespace seraph
 
 extern "C" {
@@ -80,6 +125,16 @@ int seraph_debug_fail_pinned_alloc(uint32_t k) {
 uint64_t seraph_debug_pinned_bytes(void) {
     const int64_t b = seraph::g_pinned_bytes.load();
     return b > 0 ? (uint64_t)b : 0u;
+}
+
+int seraph_debug_l2_setaside(uint64_t* bytes) {
+    return guarded([&] {
+        SR_CHECK(bytes, SERAPH_EINVAL, "bytes must not be NULL");
+        size_t v = 0;
+        SR_CUDA(cudaDeviceGetLimit(&v, cudaLimitPersistingL2CacheSize));
+        *bytes = v;
+        return SERAPH_OK;
+    });
 }
 
 int seraph_graph_from_edges(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
@@ -230,6 +285,7 @@ int seraph_graph_release_buffers(seraph_graph* g) {
         std::lock_guard<std::mutex> lk(g->ws.m);
         SR_CUDA(cudaSetDevice(g->device));
         g->ws.release();
+        seraph::l2_setaside_drop(g);
         return SERAPH_OK;
     });
 }
@@ -238,6 +294,7 @@ void seraph_graph_free(seraph_graph* g) {
     if (!g) return;
     try {
         cudaSetDevice(g->device);
+        seraph::l2_setaside_drop(g);
         delete g;
     } catch (...) {
     }

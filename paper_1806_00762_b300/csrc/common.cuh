@@ -67,6 +67,15 @@ struct PersistingL2 {
     }
 };
 
+// The context's persisting-L2 set-aside for the evict-last hot range, held
+// by the graphs whose runs use it: raised (only ever grown) on a run's
+// first need, and put back to the context's earlier value -- persisting
+// lines demoted first -- when the last holder lets go (graph freed or its
+// buffers released).  A run that finds it raised calls nothing, so it never
+// waits on work in flight elsewhere in the context.
+void l2_setaside_hold(const void* holder, int device, uint64_t bytes);
+void l2_setaside_drop(const void* holder);
+
 // Device allocation owned by the library.
 template <class T>
 struct DevBuf {
@@ -123,7 +132,15 @@ struct PinnedBuf {
         p = nullptr;
         bytes = 0;
     }
+    PinnedBuf() = default;
     ~PinnedBuf() { release(); }
+    PinnedBuf(const PinnedBuf&) = delete;
+    PinnedBuf& operator=(const PinnedBuf&) = delete;
+    PinnedBuf(PinnedBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    PinnedBuf& operator=(PinnedBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
     // The device address of a mapped allocation (an error, not a device
     // fault, if it is not mapped); null for an empty buffer.
     template <class T>

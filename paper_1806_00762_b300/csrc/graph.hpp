@@ -18,10 +18,13 @@ struct RunWorkspace {
     seraph::DevBuf<float> x, contrib, x_next, x_prev, inv_out;
     seraph::DevBuf<uint8_t> state;
     seraph::DevBuf<uint32_t> stamp, front0, front1, big;  // push stage
+    seraph::DevBuf<uint8_t> small;               // a run's small device buffers, carved
+    seraph::PinnedBuf small_h;                   // its small pinned read-back buffers
     void release() {
         ebuf.release(); lists.release(); val.release(); out.release(); x.release();
         contrib.release(); x_next.release(); x_prev.release(); inv_out.release(); state.release();
         stamp.release(); front0.release(); front1.release(); big.release();
+        small.release(); small_h.release();
     }
 };
 

@@ -51,6 +51,12 @@ struct Chunk {
     uint64_t pk_bytes, stage_off;
 };
 
+// A typed piece of a larger allocation (not owned).
+template <class T>
+struct Slice {
+    T* p = nullptr;
+};
+
 // Bytes a page stages in its slot when its chunk streams compact: its
 // streamed header, then its gap stream padded to 16 bytes.
 uint64_t staged_bytes(const PageMeta& pm) { return pm.sh_bytes + align_up(pm.pk_data, 16); }
@@ -202,7 +208,6 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     SR_CHECK(P->thread_max_deg <= P->group4_max_deg && P->group4_max_deg <= P->group8_max_deg &&
                  P->group8_max_deg <= P->warp_max_deg,
              SERAPH_EINVAL, "need thread_max_deg <= group4_max_deg <= group8_max_deg <= warp_max_deg");
-    PersistingL2 l2_guard;  // restores the context's persisting-L2 limit on every exit
     const bool learned = P->sched == SERAPH_SCHED_LEARNED;
     seraph_trace* trace = (seraph_trace*)P->trace;
     SR_CHECK(P->sched == SERAPH_SCHED_FIXED || learned, SERAPH_EINVAL, "bad sched");
@@ -358,11 +363,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     DevBuf<float> x, contrib, x_next, x_prev, inv_out;
     DevBuf<uint8_t> state;
     DevBuf<uint32_t> stamp, front0, front1, big;
+    DevBuf<uint8_t> small;
+    PinnedBuf small_h;
     // borrow the graph's kept buffers for this run (given back on every exit)
     struct Lease {
         RunWorkspace* ws = nullptr;
         DevBuf<uint8_t>* ebuf; DevBuf<unsigned long long>* lists; DevBuf<uint32_t>* val;
         DevBuf<uint32_t>* out; DevBuf<float>* f[5]; DevBuf<uint8_t>* state; DevBuf<uint32_t>* pu[4];
+        DevBuf<uint8_t>* small; PinnedBuf* small_h;
         ~Lease() {
             if (!ws) return;
             ws->ebuf = std::move(*ebuf); ws->lists = std::move(*lists); ws->val = std::move(*val);
@@ -371,10 +379,11 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             ws->inv_out = std::move(*f[4]); ws->state = std::move(*state);
             ws->stamp = std::move(*pu[0]); ws->front0 = std::move(*pu[1]);
             ws->front1 = std::move(*pu[2]); ws->big = std::move(*pu[3]);
+            ws->small = std::move(*small); ws->small_h = std::move(*small_h);
             ws->m.unlock();
         }
     } lease{nullptr, &ebuf, &lists, &val, &caller_order, {&x, &contrib, &x_next, &x_prev, &inv_out}, &state,
-            {&stamp, &front0, &front1, &big}};
+            {&stamp, &front0, &front1, &big}, &small, &small_h};
     if (g->ws.m.try_lock()) {
         RunWorkspace& w = g->ws;
         ebuf = std::move(w.ebuf); lists = std::move(w.lists); val = std::move(w.val);
@@ -383,28 +392,47 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         state = std::move(w.state);
         stamp = std::move(w.stamp); front0 = std::move(w.front0); front1 = std::move(w.front1);
         big = std::move(w.big);
+        small = std::move(w.small); small_h = std::move(w.small_h);
         lease.ws = &w;
     }
     auto ensure = [](auto& buf, size_t count) { if (buf.n < count) buf.alloc(count); };
     ensure(ebuf, slot_bytes * nslots);
-    DevBuf<PageLoc> loc(g->num_pages);
-    DevBuf<uint64_t> d_rel_soff(g->num_pages), d_rel_woff(g->num_pages), d_offb(g->num_pages);
+    // The run's small buffers, carved out of one device and one pinned
+    // allocation kept with the graph: after a graph's first run nothing is
+    // allocated, so a run issued while other work (say the read-back of the
+    // previous run's values) is in flight does not wait for it.
+    const int nparts = device_sms() * 4;
+    const uint64_t big_cap = std::min<uint64_t>(n, g->m / kPushWarpMax + 1);
+    uint64_t dsz = 0, hsz = 0;
+    auto carve = [](uint64_t& at, uint64_t bytes) { const uint64_t o = at; at = align_up(at + bytes, 256); return o; };
+    const uint64_t o_loc = carve(dsz, sizeof(PageLoc) * g->num_pages);
+    const uint64_t o_rel = carve(dsz, 3 * 8ull * g->num_pages);
+    const uint64_t o_rs = carve(dsz, sizeof(RunState));
+    const uint64_t o_rep = carve(dsz, sizeof(SweepReport));
+    const uint64_t o_steps = carve(dsz, 4ull * ring);
+    const uint64_t o_part = carve(dsz, 3 * 8ull * nparts);
+    const uint64_t o_dirty = carve(dsz, 32 * 4);
+    const uint64_t o_ps = carve(dsz, sizeof(PushState));
+    const uint64_t oh_rep = carve(hsz, sizeof(SweepReport));
+    const uint64_t oh_steps = carve(hsz, 4ull * ring);
+    const uint64_t oh_ps = carve(hsz, sizeof(PushState));
+    ensure(small, dsz);
+    if (small_h.bytes < hsz) small_h.alloc(hsz);
+    Slice<PageLoc> loc{(PageLoc*)(small.p + o_loc)};
+    Slice<uint64_t> d_rel_soff{(uint64_t*)(small.p + o_rel)};
+    Slice<uint64_t> d_rel_woff{d_rel_soff.p + g->num_pages}, d_offb{d_rel_soff.p + 2 * g->num_pages};
     SR_CUDA(cudaMemcpyAsync(d_rel_soff.p, rel_soff.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
     SR_CUDA(cudaMemcpyAsync(d_rel_woff.p, rel_woff.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
     SR_CUDA(cudaMemcpyAsync(d_offb.p, offb.data(), 8 * g->num_pages, cudaMemcpyHostToDevice, cs.s));
     ensure(lists, (uint64_t)kClasses * max_win_v);
-    DevBuf<RunState> rs(1);
-    DevBuf<SweepReport> d_rep(1);
-    DevBuf<unsigned> d_steps(ring);
+    Slice<RunState> rs{(RunState*)(small.p + o_rs)};
+    Slice<SweepReport> d_rep{(SweepReport*)(small.p + o_rep)};
+    Slice<unsigned> d_steps{(unsigned*)(small.p + o_steps)};
     SR_CUDA(cudaMemsetAsync(d_steps.p, 0, ring * sizeof(unsigned), cs.s));
-    PinnedBuf h_rep, h_steps;
-    h_rep.alloc(sizeof(SweepReport));
-    h_steps.alloc(ring * sizeof(unsigned));
-    const int nparts = device_sms() * 4;
-    DevBuf<double> partial;
+    Slice<uint8_t> h_rep{small_h.p + oh_rep}, h_steps{small_h.p + oh_steps}, h_ps{small_h.p + oh_ps};
+    Slice<double> partial{(double*)(small.p + o_part)};
     if (is_pr) {
         ensure(x, n); ensure(contrib, n); ensure(x_next, n); ensure(x_prev, n); ensure(inv_out, n);
-        partial.alloc(3 * nparts);
     } else {
         ensure(val, n);
     }
@@ -412,19 +440,14 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
     const bool push_on = P->push != 0;
     SR_CHECK(P->count_clean <= 1, SERAPH_EINVAL, "count_clean must be 0 or 1");
     const bool count_clean = P->count_clean != 0 && !is_pr;
-    DevBuf<uint32_t> dirty_blocks;
-    if (count_clean) dirty_blocks.alloc(32);
-    const uint64_t big_cap = std::min<uint64_t>(n, g->m / kPushWarpMax + 1);
-    DevBuf<PushState> d_ps;
-    PinnedBuf h_ps;
+    Slice<uint32_t> dirty_blocks{count_clean ? (uint32_t*)(small.p + o_dirty) : nullptr};
+    Slice<PushState> d_ps{push_on ? (PushState*)(small.p + o_ps) : nullptr};
     if (push_on || count_clean) {
         ensure(stamp, n);
         SR_CUDA(cudaMemsetAsync(stamp.p, 0, n * sizeof(uint32_t), cs.s));
     }
     if (push_on) {
         ensure(front0, n); ensure(front1, n); ensure(big, big_cap);
-        d_ps.alloc(1);
-        h_ps.alloc(sizeof(PushState));
     }
     const uint64_t push_below = P->push_below ? P->push_below : std::max<uint64_t>(n / 256, 1);
 
@@ -472,7 +495,7 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         a.hot = (uint32_t)std::min<uint64_t>(n, hot_bytes / 4);
         // set-aside = the hot range (measured: a larger set-aside starves the
         // normal lines -- 5/3 of 48 MB cost 8 % of PageRank's relax time)
-        if (a.hints) l2_guard.reserve(g->device, (uint64_t)a.hot * 4);
+        if (a.hints) l2_setaside_hold(g, g->device, (uint64_t)a.hot * 4);
     }
 
     uint64_t launches = 0;
@@ -487,8 +510,11 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             launches += 3;
         } else {
             uint32_t source = P->source;
-            if (g->reordered && algo != SERAPH_CC)  // the caller's source id -> internal id
-                SR_CUDA(cudaMemcpy(&source, g->d_inv.p + source, 4, cudaMemcpyDeviceToHost));
+            if (g->reordered && algo != SERAPH_CC) {  // the caller's source id -> internal id
+                SR_CUDA(cudaMemcpyAsync(h_steps.p, g->d_inv.p + source, 4, cudaMemcpyDeviceToHost, cs.s));
+                SR_CUDA(cudaStreamSynchronize(cs.s));
+                std::memcpy(&source, h_steps.p, 4);
+            }
             launch_init_values(algo, a, n, source, g->reordered ? g->d_perm.p : nullptr, cs.s);
             launches += 1;
         }

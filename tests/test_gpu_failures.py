@@ -78,11 +78,14 @@ def test_failed_pinned_allocation_in_graph_build_returns_enomem_and_keeps_nothin
 
 
 def test_failed_pinned_allocation_in_a_run_returns_enomem_and_next_run_is_exact(r14):
+    """A graph's first run pins its small read-back buffers (kept with the
+    graph): failing that allocation gives SERAPH_ENOMEM and keeps nothing.
+    Once a run has succeeded, later runs allocate nothing, so an armed
+    failure does not touch them."""
     n, src, dst, w, og = r14
+    base = seraph.debug_pinned_bytes()
     g = seraph.Graph.from_edges(n, src, dst, w, num_pages=8)
     ref = oracle.sssp(og, 0)
-    dist, _ = seraph.run(g, "sssp", source=0, budget_bytes=1 << 20)
-    assert np.array_equal(dist, ref)
     pinned0 = seraph.debug_pinned_bytes()
     seraph.debug_fail_pinned_alloc(1)
     try:
@@ -94,7 +97,17 @@ def test_failed_pinned_allocation_in_a_run_returns_enomem_and_next_run_is_exact(
     assert seraph.debug_pinned_bytes() == pinned0
     dist, st = seraph.run(g, "sssp", source=0, budget_bytes=1 << 20)
     assert st["converged"] == 1 and np.array_equal(dist, ref)
+    pinned1 = seraph.debug_pinned_bytes()
+    seraph.debug_fail_pinned_alloc(1)
+    try:
+        dist, _ = seraph.run(g, "sssp", source=0, budget_bytes=1 << 20)
+        x, _ = seraph.run(g, "bfs", source=0, budget_bytes=1 << 20)
+    finally:
+        seraph.debug_fail_pinned_alloc(0)
+    assert np.array_equal(dist, ref) and np.array_equal(x, oracle.bfs(og, 0))
+    assert seraph.debug_pinned_bytes() == pinned1
     g.free()
+    assert seraph.debug_pinned_bytes() == base
 
 
 def test_from_csr_rejects_bad_device_offsets(r14):
