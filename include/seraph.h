@@ -591,6 +591,30 @@ int  seraph_batch_run(seraph_bgraph* const* graphs, uint32_t ng, const seraph_qu
                       uint32_t nq, int out_mem, const seraph_batch_params* p,
                       seraph_batch_stats* stats);
 
+/* A prepared batch for serving loops: the same queries (sources may change)
+ * run again and again without re-planning.  seraph_batch_plan_create does
+ * what seraph_batch_run does before its launch -- checks, autotuning (cached
+ * in the graphs), grouping, the device tables, the per-query arrays, the
+ * captured launch when params.use_graph -- once; every queries[i].out must be
+ * a caller-owned DEVICE array of n_graph uint32, written by every run (the
+ * caller reads it back however it likes, e.g. on its own stream while the
+ * next run computes).  The graphs must outlive the plan; params.replays is
+ * ignored (one launch per run); runs go to params.stream (NULL = the plan's
+ * own) and must not overlap.
+ * seraph_batch_plan_run: one launch; `sources` (host, nq values, NULL = as
+ * before) replaces the queries' sources first (checked against n; SERAPH_EINVAL
+ * with nothing run otherwise).  It allocates nothing unless new sources change
+ * a group's round-0 task count (a tile smaller than the group with repeated
+ * sources), when the plan is rebuilt.  Returns after the launch completes;
+ * stats as for seraph_batch_run (tune_ms 0).  Errors as seraph_batch_run. */
+typedef struct seraph_batch_plan seraph_batch_plan;
+int  seraph_batch_plan_create(seraph_bgraph* const* graphs, uint32_t ng,
+                              const seraph_query* queries, uint32_t nq,
+                              const seraph_batch_params* p, seraph_batch_plan** plan);
+int  seraph_batch_plan_run(seraph_batch_plan* plan, const uint32_t* sources,
+                           seraph_batch_stats* stats);
+void seraph_batch_plan_free(seraph_batch_plan* plan);
+
 /*
  * Host-side fault injection and accounting, for tests of the failure paths
  * (not in the paper).  Every failure is made on the host; nothing here makes

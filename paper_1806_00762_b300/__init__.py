@@ -390,3 +390,71 @@ def batch_run(graphs, queries, outs=None, stream=None, **kw):
     stats["mapping"] = list(st.mapping)[:len(graphs)]
     stats["tile"] = list(st.tile)[:len(graphs)]
     return outs, stats
+
+
+def _batch_params(kw, stream):
+    p = C.BatchParams()
+    C.check(C.lib().seraph_batch_params_default(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k == "mapping" and isinstance(v, str):
+            v = C.MAPPINGS[v]
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    p.stream = _stream_ptr(stream)
+    return p
+
+
+def _batch_stats(st, ng):
+    stats = {k: getattr(st, k) for k, _ in st._fields_ if k not in ("mapping", "tile")}
+    stats["mapping"] = list(st.mapping)[:ng]
+    stats["tile"] = list(st.tile)[:ng]
+    return stats
+
+
+class BatchPlan:
+    """A prepared batch (seraph_batch_plan_*): queries [(graph index,
+    "bfs"|"sssp", source), ...] with one caller-owned CUDA uint32/int32 tensor
+    per query, planned once (autotuning, grouping, device tables, captured
+    launch) and run any number of times; each run writes the outputs."""
+
+    def __init__(self, graphs, queries, outs, stream=None, **kw):
+        p = _batch_params(kw, stream)
+        arr = (C.Query * len(queries))()
+        for i, ((g, algo, src), o) in enumerate(zip(queries, outs)):
+            po, mo, _ = _ptr_mem(o)
+            if mo != C.MEM_DEVICE:
+                raise ValueError("plan outputs must be device arrays")
+            arr[i] = C.Query(g, C.ALGOS.get(algo, -1) if isinstance(algo, str) else algo, src, 0, po)
+        hs = (ctypes.c_void_p * len(graphs))(*[g._h.value for g in graphs])
+        h = ctypes.c_void_p()
+        C.check(C.lib().seraph_batch_plan_create(hs, len(graphs), arr, len(queries), ctypes.byref(p),
+                                                 ctypes.byref(h)))
+        self._h = h
+        self._keep = (graphs, outs)
+        self.nq = len(queries)
+        self.ng = len(graphs)
+
+    def run(self, sources=None) -> dict:
+        """One launch; `sources` (nq values) replaces the queries' sources."""
+        src = None
+        if sources is not None:
+            src = np.ascontiguousarray(sources, dtype=np.uint32)
+            if src.shape != (self.nq,):
+                raise ValueError("one source per query")
+        st = C.BatchStats()
+        C.check(C.lib().seraph_batch_plan_run(self._h, None if src is None else src.ctypes.data,
+                                              ctypes.byref(st)))
+        return _batch_stats(st, self.ng)
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            C.lib().seraph_batch_plan_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+

@@ -145,6 +145,10 @@ PROTOTYPES = {
     "seraph_batch_params_default": (ctypes.c_int, [ctypes.POINTER(BatchParams)]),
     "seraph_batch_run": (ctypes.c_int, [vp, u32, vp, u32, ctypes.c_int,
                                         ctypes.POINTER(BatchParams), ctypes.POINTER(BatchStats)]),
+    "seraph_batch_plan_create": (ctypes.c_int, [vp, u32, vp, u32, ctypes.POINTER(BatchParams),
+                                                ctypes.POINTER(vp)]),
+    "seraph_batch_plan_run": (ctypes.c_int, [vp, vp, ctypes.POINTER(BatchStats)]),
+    "seraph_batch_plan_free": (None, [vp]),
     "seraph_debug_fail_pinned_alloc": (ctypes.c_int, [u32]),
     "seraph_debug_pinned_bytes": (u64, []),
     "seraph_debug_l2_setaside": (ctypes.c_int, [ctypes.POINTER(u64)]),

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -887,15 +888,63 @@ void wait_stream(cudaStream_t s, uint32_t timeout_ms) {
     }
 }
 
-// One batched launch over `qs` (distances stay in q.out when given, else in
-// scratch); `replays` timed repetitions, through a captured CUDA graph if
-// `use_graph`.  Distances of the last repetition are left in `dist_out[q]`.
-Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vector<QSpec>& qs,
-                     bool use_graph, uint32_t replays, uint32_t timeout_ms, cudaStream_t s,
-                     std::vector<uint32_t*>* dist_out, std::vector<DevBuf<uint32_t>>* hold,
-                     bool group = false) {
+// Everything one batched launch needs on the device, built once and run any
+// number of times (a plan keeps it between calls): the record tables, the
+// per-query arrays carved from one pool, the task ring, the captured launch.
+struct Prepared {
+    std::vector<BGraphDev> gd;
+    std::vector<std::vector<uint32_t>> recs;  // the queries of each record
+    std::vector<BQuery> qh;
+    std::vector<BGroupIO> ioh;
+    std::vector<DevBuf<uint32_t>> hold;       // the per-query array pool
+    DevBuf<BGraphDev> d_g;
+    DevBuf<BQuery> d_q;
+    DevBuf<BGroupIO> d_io;
+    DevBuf<uint2> d_t0;
+    DevBuf<BGlobal> d_gl;
+    DevBuf<TaskSlot> d_ring;
+    PinnedBuf gl_h;                           // the counters read back after a run
+    PinnedBuf tab_h;                          // record tables staged for upload
+    unsigned long long cap = 0, spin_limit = 0;
+    unsigned blocks = 0;
+    uint32_t nr = 0, ntask0 = 0, max_n = 1, timeout_ms = 0;
+    bool any_group = false, captured = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Prepared() = default;
+    Prepared(const Prepared&) = delete;
+    Prepared& operator=(const Prepared&) = delete;
+    ~Prepared() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    void enqueue(cudaStream_t st) const {
+        const dim3 ig((max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64, std::min<uint32_t>(nr, 65535));
+        init_dist_kernel<<<ig, 256, 0, st>>>(d_q.p, d_io.p, d_g.p, nr);
+        init_queries_kernel<<<(unsigned)std::min<unsigned long long>((cap + 255) / 256, 4096), 256, 0, st>>>(
+            d_q.p, d_io.p, nr, d_gl.p, d_ring.p, cap, d_t0.p, ntask0);
+        batch_kernel<<<blocks, kNT, 0, st>>>(d_g.p, d_q.p, d_gl.p, d_ring.p, cap - 1, spin_limit);
+        if (any_group) group_scatter_kernel<<<ig, 256, 0, st>>>(d_q.p, d_io.p, d_g.p, nr);
+    }
+    // The record tables (as built, or with new sources) to the device on `st`.
+    void upload(cudaStream_t st) {
+        const size_t qb = nr * sizeof(BQuery), ib = nr * sizeof(BGroupIO);
+        std::memcpy(tab_h.p, qh.data(), qb);
+        std::memcpy(tab_h.p + qb, ioh.data(), ib);
+        SR_CUDA(cudaMemcpyAsync(d_q.p, tab_h.p, qb, cudaMemcpyHostToDevice, st));
+        SR_CUDA(cudaMemcpyAsync(d_io.p, tab_h.p + qb, ib, cudaMemcpyHostToDevice, st));
+    }
+};
+
+// Builds `pb` for the queries `qs` (distances stay in q.out when given, else
+// in the pool; `dist_out[q]` says where) and captures its launch in a CUDA
+// graph if `use_graph`.
+void prepare_batch(Prepared& pb, const std::vector<seraph_bgraph*>& graphs,
+                   const std::vector<QSpec>& qs, bool use_graph, uint32_t timeout_ms, cudaStream_t s,
+                   std::vector<uint32_t*>* dist_out, bool group) {
     const uint32_t nq = (uint32_t)qs.size();
-    std::vector<BGraphDev> gd(graphs.size());
+    std::vector<BGraphDev>& gd = pb.gd;
+    gd.assign(graphs.size(), BGraphDev{});
     for (size_t i = 0; i < graphs.size(); ++i) {
         const seraph_bgraph* g = graphs[i];
         gd[i] = BGraphDev{g->adj.off.p, g->adj.col.p, g->weighted ? g->adj.wptr() : nullptr,
@@ -904,7 +953,8 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
     // Records: with `group`, the queries of one graph, algorithm and tuning
     // (tile, near-far width, pull threshold) run in lockstep groups of up to
     // kMaxGroup; otherwise (and for a query left alone) one record each.
-    std::vector<std::vector<uint32_t>> recs;
+    std::vector<std::vector<uint32_t>>& recs = pb.recs;
+    recs.clear();
     {
         std::vector<uint8_t> taken(nq, 0);
         for (uint32_t q = 0; q < nq; ++q) {
@@ -923,8 +973,10 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
         }
     }
     const uint32_t nr = (uint32_t)recs.size();
-    std::vector<BQuery> qh(nr);
-    std::vector<BGroupIO> ioh(nr);
+    pb.qh.assign(nr, BQuery{});
+    pb.ioh.assign(nr, BGroupIO{});
+    std::vector<BQuery>& qh = pb.qh;
+    std::vector<BGroupIO>& ioh = pb.ioh;
     std::vector<uint2> init_tasks;  // (record, tile) of every round-0 task
     // every per-query array comes out of one allocation (one cudaMalloc per
     // call instead of several per query), each array 128-byte aligned
@@ -941,9 +993,9 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
             for (uint32_t q : r) pool_words += qs[q].out ? 0 : words(n);
         }
     }
-    hold->clear();
-    hold->emplace_back(std::max<uint64_t>(pool_words, 1));
-    uint32_t* pool = hold->back().p;
+    pb.hold.clear();
+    pb.hold.emplace_back(std::max<uint64_t>(pool_words, 1));
+    uint32_t* pool = pb.hold.back().p;
     auto carve = [&](uint64_t n) { uint32_t* p = pool; pool += words(n); return p; };
     uint64_t tiles = 0;
     uint32_t max_n = 1;
@@ -1004,54 +1056,61 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
     unsigned long long cap = 1024;
     const uint32_t ntask0 = (uint32_t)init_tasks.size();
     while (cap < tiles + ntask0 + 4ull * blocks + 1024) cap <<= 1;
-    DevBuf<BGraphDev> d_g(gd.size());
-    DevBuf<BQuery> d_q(nr);
-    DevBuf<BGroupIO> d_io(nr);
-    DevBuf<uint2> d_t0(ntask0);
-    DevBuf<BGlobal> d_gl(1);
-    DevBuf<TaskSlot> d_ring(cap);
-    SR_CUDA(cudaMemcpyAsync(d_g.p, gd.data(), gd.size() * sizeof(BGraphDev), cudaMemcpyHostToDevice, s));
-    SR_CUDA(cudaMemcpyAsync(d_q.p, qh.data(), nr * sizeof(BQuery), cudaMemcpyHostToDevice, s));
-    SR_CUDA(cudaMemcpyAsync(d_io.p, ioh.data(), nr * sizeof(BGroupIO), cudaMemcpyHostToDevice, s));
-    SR_CUDA(cudaMemcpyAsync(d_t0.p, init_tasks.data(), ntask0 * sizeof(uint2), cudaMemcpyHostToDevice, s));
+    pb.nr = nr;
+    pb.ntask0 = ntask0;
+    pb.cap = cap;
+    pb.blocks = blocks;
+    pb.max_n = max_n;
+    pb.any_group = any_group;
+    pb.timeout_ms = timeout_ms;
     // ~15 polls per microsecond with the back-off: a limit of timeout_ms
-    const unsigned long long spin_limit = (unsigned long long)timeout_ms * 15000ull;
-    auto enqueue = [&](cudaStream_t st) {
-        const dim3 ig((max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64, std::min<uint32_t>(nr, 65535));
-        init_dist_kernel<<<ig, 256, 0, st>>>(d_q.p, d_io.p, d_g.p, nr);
-        init_queries_kernel<<<(unsigned)std::min<unsigned long long>((cap + 255) / 256, 4096), 256, 0, st>>>(
-            d_q.p, d_io.p, nr, d_gl.p, d_ring.p, cap, d_t0.p, ntask0);
-        batch_kernel<<<blocks, kNT, 0, st>>>(d_g.p, d_q.p, d_gl.p, d_ring.p, cap - 1, spin_limit);
-        if (any_group) group_scatter_kernel<<<ig, 256, 0, st>>>(d_q.p, d_io.p, d_g.p, nr);
-    };
-    Outcome out;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    pb.spin_limit = (unsigned long long)timeout_ms * 15000ull;
+    pb.d_g.alloc(gd.size());
+    pb.d_q.alloc(nr);
+    pb.d_io.alloc(nr);
+    pb.d_t0.alloc(ntask0);
+    pb.d_gl.alloc(1);
+    pb.d_ring.alloc(cap);
+    pb.gl_h.alloc(sizeof(BGlobal));
+    pb.tab_h.alloc(nr * (sizeof(BQuery) + sizeof(BGroupIO)));
+    SR_CUDA(cudaMemcpyAsync(pb.d_g.p, gd.data(), gd.size() * sizeof(BGraphDev), cudaMemcpyHostToDevice, s));
+    pb.upload(s);
+    SR_CUDA(cudaMemcpyAsync(pb.d_t0.p, init_tasks.data(), ntask0 * sizeof(uint2), cudaMemcpyHostToDevice, s));
+    SR_CUDA(cudaStreamSynchronize(s));  // (the staged tables are reused by later uploads)
     if (use_graph) {
         SR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        enqueue(s);
-        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        if (ce == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
-            out.captured = true;
+        pb.enqueue(s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &pb.graph);
+        if (ce == cudaSuccess && cudaGraphInstantiate(&pb.exec, pb.graph, 0) == cudaSuccess) {
+            pb.captured = true;
         } else {
             (void)cudaGetLastError();
-            if (graph) cudaGraphDestroy(graph);
-            graph = nullptr;
+            if (pb.graph) cudaGraphDestroy(pb.graph);
+            pb.graph = nullptr;
         }
     }
+}
+
+// `replays` timed runs of a prepared batch (through its captured graph when
+// there is one); the distances of the last are left in the queries' arrays.
+// Allocates nothing.
+Outcome run_batch(Prepared& pb, uint32_t replays, cudaStream_t s) {
+    Outcome out;
+    out.captured = pb.captured;
     cudaEvent_t e0, e1;
     SR_CUDA(cudaEventCreate(&e0));
     SR_CUDA(cudaEventCreate(&e1));
     const uint32_t reps = std::max<uint32_t>(replays, 1);
     SR_CUDA(cudaEventRecord(e0, s));
     for (uint32_t r = 0; r < reps; ++r) {
-        if (out.captured) SR_CUDA(cudaGraphLaunch(exec, s));
-        else enqueue(s);
+        if (pb.captured) SR_CUDA(cudaGraphLaunch(pb.exec, s));
+        else pb.enqueue(s);
         SR_LAUNCH();
     }
     SR_CUDA(cudaEventRecord(e1, s));
+    SR_CUDA(cudaMemcpyAsync(pb.gl_h.p, pb.d_gl.p, sizeof(BGlobal), cudaMemcpyDeviceToHost, s));
     try {
-        wait_stream(s, timeout_ms * reps + 1000);
+        wait_stream(s, pb.timeout_ms * reps + 1000);
     } catch (...) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1061,10 +1120,8 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
     SR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
     BGlobal gl;
-    SR_CUDA(cudaMemcpy(&gl, d_gl.p, sizeof(gl), cudaMemcpyDeviceToHost));
+    std::memcpy(&gl, pb.gl_h.p, sizeof(gl));
     SR_CHECK(gl.err == 0, SERAPH_ETIMEOUT, "batched kernel: a bounded wait ran out (status " +
                                                std::to_string(gl.err) + ")");
     out.ms = ms / reps;
@@ -1072,6 +1129,14 @@ Outcome launch_batch(const std::vector<seraph_bgraph*>& graphs, const std::vecto
     out.tasks = gl.tasks;
     out.max_round = gl.max_round;
     return out;
+}
+
+// One batched launch: prepare, then run `replays` times.
+Outcome launch_batch(Prepared& pb, const std::vector<seraph_bgraph*>& graphs, const std::vector<QSpec>& qs,
+                     bool use_graph, uint32_t replays, uint32_t timeout_ms, cudaStream_t s,
+                     std::vector<uint32_t*>* dist_out, bool group = false) {
+    prepare_batch(pb, graphs, qs, use_graph, timeout_ms, s, dist_out, group);
+    return run_batch(pb, replays, s);
 }
 
 }  // namespace
@@ -1091,27 +1156,27 @@ void bgraph_build(seraph_bgraph* g, uint64_t n, uint64_t m, const uint32_t* src,
     sorted_adjacency(n, m, src, dst, nullptr, mem, false, s, g->in_adj);
 }
 
-int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* qin, uint32_t nq,
-              int out_mem, const seraph_batch_params* P, seraph_batch_stats* st) {
-    SR_CHECK(graphs_in && qin && P && ng >= 1 && nq >= 1, SERAPH_EINVAL, "bad batch arguments");
-    SR_CHECK(out_mem == SERAPH_MEM_HOST || out_mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad out_mem");
-    SR_CHECK(P->mapping >= SERAPH_MAP_AUTO && P->mapping <= SERAPH_MAP_CTA, SERAPH_EINVAL, "bad mapping");
-    SR_CHECK(P->tile == 0 || (P->tile <= (1u << 20)), SERAPH_EINVAL, "bad tile");
+namespace {
+
+// The launch specs of a batch call: each graph's mapping, tile and near-far
+// width -- fixed, cached in the graph, or autotuned on the graph's own
+// queries -- then one spec per query (checked).  S.tune_ms gets the tuning
+// time; gmap / gtile the choices.
+std::vector<QSpec> batch_specs(const std::vector<seraph_bgraph*>& graphs, const seraph_query* qin,
+                               uint32_t nq, int out_mem, const seraph_batch_params* P, cudaStream_t s,
+                               seraph_batch_stats& S, std::vector<uint32_t>& gmap,
+                               std::vector<uint32_t>& gtile) {
+    const uint32_t ng = (uint32_t)graphs.size();
     // 0 = a width per graph (tuned below with the mapping), else the caller's
     const uint32_t delta = P->delta ? P->delta : kDefaultDelta;
     const bool tune_delta = P->delta == 0 && P->mapping == SERAPH_MAP_AUTO;
     const uint32_t pull_div = P->bfs_pull_div ? P->bfs_pull_div : kDefaultPullDiv;
-    SR_CHECK(P->group <= 1, SERAPH_EINVAL, "group must be 0 or 1");
     const bool group = P->group != 0;
-    std::vector<seraph_bgraph*> graphs(graphs_in, graphs_in + ng);
-    for (auto* g : graphs) SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
-    SR_CUDA(cudaSetDevice(graphs[0]->device));
-    Stream s;
-    s.use(P->stream);
-    seraph_batch_stats S{};
     auto t_tune = std::chrono::steady_clock::now();
     // per-graph mapping and tile: fixed, cached, or autotuned on the graph's own queries
-    std::vector<uint32_t> gmap(ng), gtile(ng), gdelta(ng, delta);
+    gmap.assign(ng, 0);
+    gtile.assign(ng, 0);
+    std::vector<uint32_t> gdelta(ng, delta);
     for (uint32_t gi = 0; gi < ng; ++gi) {
         if (P->mapping != SERAPH_MAP_AUTO) {
             gmap[gi] = (uint32_t)P->mapping;
@@ -1142,8 +1207,8 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
             for (uint32_t mp : maps)
                 for (uint32_t tl : tls) {
                     for (auto& x : sub) { x.mapping = mp; x.tile = tl; }
-                    std::vector<DevBuf<uint32_t>> hold;
-                    const Outcome o = launch_batch(one, sub, false, 2, P->timeout_ms, s.s, nullptr, &hold,
+                    Prepared pb;
+                    const Outcome o = launch_batch(pb, one, sub, false, 2, P->timeout_ms, s, nullptr,
                                                    group);
                     if (o.ms < best) { best = o.ms; bm = mp; bt = tl; }
                 }
@@ -1157,8 +1222,8 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
             float bestd = 1e30f;
             for (uint32_t d : {64u, 128u, 256u, 512u}) {
                 for (auto& x : ss) { x.mapping = bm; x.tile = bt; x.delta = d; }
-                std::vector<DevBuf<uint32_t>> hold;
-                const Outcome o = launch_batch(one, ss, false, 2, P->timeout_ms, s.s, nullptr, &hold, group);
+                Prepared pb;
+                const Outcome o = launch_batch(pb, one, ss, false, 2, P->timeout_ms, s, nullptr, group);
                 if (o.ms < bestd) { bestd = o.ms; bd = d; }
             }
         }
@@ -1184,9 +1249,30 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
         qs[q] = QSpec{Q.graph, algo, Q.source, gmap[Q.graph], tile,
                       out_mem == SERAPH_MEM_DEVICE ? Q.out : nullptr, gdelta[Q.graph], pull_div};
     }
+    return qs;
+}
+
+}  // namespace
+
+int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* qin, uint32_t nq,
+              int out_mem, const seraph_batch_params* P, seraph_batch_stats* st) {
+    SR_CHECK(graphs_in && qin && P && ng >= 1 && nq >= 1, SERAPH_EINVAL, "bad batch arguments");
+    SR_CHECK(out_mem == SERAPH_MEM_HOST || out_mem == SERAPH_MEM_DEVICE, SERAPH_EINVAL, "bad out_mem");
+    SR_CHECK(P->mapping >= SERAPH_MAP_AUTO && P->mapping <= SERAPH_MAP_CTA, SERAPH_EINVAL, "bad mapping");
+    SR_CHECK(P->tile == 0 || (P->tile <= (1u << 20)), SERAPH_EINVAL, "bad tile");
+    SR_CHECK(P->group <= 1, SERAPH_EINVAL, "group must be 0 or 1");
+    const bool group = P->group != 0;
+    std::vector<seraph_bgraph*> graphs(graphs_in, graphs_in + ng);
+    for (auto* g : graphs) SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
+    SR_CUDA(cudaSetDevice(graphs[0]->device));
+    Stream s;
+    s.use(P->stream);
+    seraph_batch_stats S{};
+    std::vector<uint32_t> gmap, gtile;
+    const std::vector<QSpec> qs = batch_specs(graphs, qin, nq, out_mem, P, s.s, S, gmap, gtile);
     std::vector<uint32_t*> dist(nq);
-    std::vector<DevBuf<uint32_t>> hold;
-    const Outcome o = launch_batch(graphs, qs, P->use_graph != 0, P->replays, P->timeout_ms, s.s, &dist, &hold,
+    Prepared pb;
+    const Outcome o = launch_batch(pb, graphs, qs, P->use_graph != 0, P->replays, P->timeout_ms, s.s, &dist,
                                    group);
     if (out_mem == SERAPH_MEM_HOST)
         for (uint32_t q = 0; q < nq; ++q)
@@ -1201,6 +1287,120 @@ int batch_run(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* 
     for (uint32_t gi = 0; gi < ng && gi < 16; ++gi) { S.mapping[gi] = gmap[gi]; S.tile[gi] = gtile[gi]; }
     if (st) *st = S;
     return SERAPH_OK;
+}
+
+}  // namespace seraph
+
+// A prepared batch (seraph_batch_plan_*): the queries' launch specs, their
+// device tables and array pool, and the captured launch, kept between runs
+// so that a run allocates nothing.
+struct seraph_batch_plan {
+    int device = 0;
+    std::vector<seraph_bgraph*> graphs;
+    std::vector<seraph::QSpec> qs;
+    std::vector<uint32_t> rec, pos;  // each query's record and place in it
+    seraph::Stream s;
+    seraph::Prepared pb;
+    seraph_batch_params P{};
+    std::vector<uint32_t> gmap, gtile;
+};
+
+namespace seraph {
+namespace {
+
+// Round-0 tiles of a group record: its distinct sources over its tile.
+uint32_t group_tiles0(const BGroupIO& io, const BQuery& b) {
+    uint32_t distinct = 0;
+    for (uint32_t j = 0; j < b.gsz; ++j) {
+        bool seen = false;
+        for (uint32_t i = 0; i < j && !seen; ++i) seen = io.src[i] == io.src[j];
+        distinct += !seen;
+    }
+    return (distinct + b.tile - 1) / b.tile;
+}
+
+}  // namespace
+
+int batch_plan_create(seraph_bgraph* const* graphs_in, uint32_t ng, const seraph_query* qin, uint32_t nq,
+                      const seraph_batch_params* P, seraph_batch_plan** out) {
+    SR_CHECK(out, SERAPH_EINVAL, "plan output must not be NULL");
+    *out = nullptr;
+    SR_CHECK(graphs_in && qin && P && ng >= 1 && nq >= 1, SERAPH_EINVAL, "bad batch arguments");
+    SR_CHECK(P->mapping >= SERAPH_MAP_AUTO && P->mapping <= SERAPH_MAP_CTA, SERAPH_EINVAL, "bad mapping");
+    SR_CHECK(P->tile == 0 || (P->tile <= (1u << 20)), SERAPH_EINVAL, "bad tile");
+    SR_CHECK(P->group <= 1, SERAPH_EINVAL, "group must be 0 or 1");
+    auto plan = std::make_unique<seraph_batch_plan>();
+    plan->graphs.assign(graphs_in, graphs_in + ng);
+    for (auto* g : plan->graphs) SR_CHECK(g != nullptr, SERAPH_EINVAL, "null graph");
+    plan->device = plan->graphs[0]->device;
+    SR_CUDA(cudaSetDevice(plan->device));
+    plan->P = *P;
+    plan->s.use(P->stream);
+    seraph_batch_stats S{};
+    plan->qs = batch_specs(plan->graphs, qin, nq, SERAPH_MEM_DEVICE, P, plan->s.s, S, plan->gmap, plan->gtile);
+    prepare_batch(plan->pb, plan->graphs, plan->qs, P->use_graph != 0, P->timeout_ms, plan->s.s, nullptr,
+                  P->group != 0);
+    plan->rec.assign(nq, 0);
+    plan->pos.assign(nq, 0);
+    for (uint32_t ri = 0; ri < plan->pb.recs.size(); ++ri)
+        for (uint32_t j = 0; j < plan->pb.recs[ri].size(); ++j) {
+            plan->rec[plan->pb.recs[ri][j]] = ri;
+            plan->pos[plan->pb.recs[ri][j]] = j;
+        }
+    *out = plan.release();
+    return SERAPH_OK;
+}
+
+int batch_plan_run(seraph_batch_plan* plan, const uint32_t* sources, seraph_batch_stats* st) {
+    SR_CHECK(plan, SERAPH_EINVAL, "null plan");
+    SR_CUDA(cudaSetDevice(plan->device));
+    Prepared& pb = plan->pb;
+    const uint32_t nq = (uint32_t)plan->qs.size();
+    if (sources) {
+        for (uint32_t q = 0; q < nq; ++q)
+            SR_CHECK(sources[q] < plan->graphs[plan->qs[q].graph]->n, SERAPH_EINVAL, "query source >= n");
+        bool same_tiles = true;
+        for (uint32_t q = 0; q < nq; ++q) {
+            plan->qs[q].source = sources[q];
+            BQuery& b = pb.qh[plan->rec[q]];
+            BGroupIO& io = pb.ioh[plan->rec[q]];
+            if (b.gsz == 1) {
+                b.source = sources[q];
+            } else {
+                io.src[plan->pos[q]] = sources[q];
+                if (plan->pos[q] == 0) b.source = sources[q];
+            }
+        }
+        for (uint32_t ri = 0; ri < pb.nr; ++ri)
+            if (pb.qh[ri].gsz > 1) same_tiles &= group_tiles0(pb.ioh[ri], pb.qh[ri]) == pb.ioh[ri].tiles0;
+        if (same_tiles) {
+            pb.upload(plan->s.s);
+        } else {  // a group's round-0 task count changed (repeated sources, small tiles): rebuild
+            prepare_batch(pb, plan->graphs, plan->qs, plan->P.use_graph != 0, plan->P.timeout_ms, plan->s.s,
+                          nullptr, plan->P.group != 0);
+        }
+    }
+    const Outcome o = run_batch(pb, 1, plan->s.s);
+    if (st) {
+        seraph_batch_stats S{};
+        S.time_ms = o.ms;
+        S.edges = o.edges;
+        S.tasks = o.tasks;
+        S.rounds_max = o.max_round;
+        S.graph_captured = o.captured;
+        for (uint32_t gi = 0; gi < plan->graphs.size() && gi < 16; ++gi) {
+            S.mapping[gi] = plan->gmap[gi];
+            S.tile[gi] = plan->gtile[gi];
+        }
+        *st = S;
+    }
+    return SERAPH_OK;
+}
+
+void batch_plan_free(seraph_batch_plan* plan) {
+    if (!plan) return;
+    cudaSetDevice(plan->device);
+    delete plan;
 }
 
 }  // namespace seraph

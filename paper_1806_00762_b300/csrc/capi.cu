@@ -20,6 +20,10 @@ void bgraph_build(seraph_bgraph* g, uint64_t n, uint64_t m, const uint32_t* src,
                   const uint32_t* dst, const uint32_t* w, int mem, cudaStream_t s);
 int batch_run(seraph_bgraph* const* graphs, uint32_t ng, const seraph_query* q, uint32_t nq,
               int out_mem, const seraph_batch_params* P, seraph_batch_stats* st);
+int batch_plan_create(seraph_bgraph* const* graphs, uint32_t ng, const seraph_query* q, uint32_t nq,
+                      const seraph_batch_params* P, seraph_batch_plan** out);
+int batch_plan_run(seraph_batch_plan* plan, const uint32_t* sources, seraph_batch_stats* st);
+void batch_plan_free(seraph_batch_plan* plan);
 }
 
 
@@ -541,6 +545,22 @@ int seraph_batch_run(seraph_bgraph* const* graphs, uint32_t ng, const seraph_que
                      uint32_t nq, int out_mem, const seraph_batch_params* p,
                      seraph_batch_stats* stats) {
     return guarded([&] { return seraph::batch_run(graphs, ng, queries, nq, out_mem, p, stats); });
+}
+
+int seraph_batch_plan_create(seraph_bgraph* const* graphs, uint32_t ng, const seraph_query* queries,
+                             uint32_t nq, const seraph_batch_params* p, seraph_batch_plan** out) {
+    return guarded([&] { return seraph::batch_plan_create(graphs, ng, queries, nq, p, out); });
+}
+
+int seraph_batch_plan_run(seraph_batch_plan* plan, const uint32_t* sources, seraph_batch_stats* stats) {
+    return guarded([&] { return seraph::batch_plan_run(plan, sources, stats); });
+}
+
+void seraph_batch_plan_free(seraph_batch_plan* plan) {
+    try {
+        seraph::batch_plan_free(plan);
+    } catch (...) {
+    }
 }
 
 }  // extern "C"
