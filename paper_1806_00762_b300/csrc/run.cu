@@ -349,7 +349,9 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
         }
         max_win_v = std::max<uint64_t>(max_win_v, s);
     }
-    uint32_t ring = 1024;
+    // step ring (per-step events, change counts and bookkeeping, indexed by
+    // step modulo its size): more steps than a sweep plus its look-ahead
+    uint32_t ring = 64;
     while (ring < 4 * (uint64_t)C + 8) ring <<= 1;
 
     // --------------------------------------------------------- allocations
