@@ -527,7 +527,7 @@ def main():
     step_no = [0]
 
     algos = args.algos.split(",")
-    empty = {k: 0 for k in ("time_ms", "wall_ms", "relax_ms", "relax_launches", "bytes_streamed",
+    empty = {k: 0 for k in ("time_ms", "wall_ms", "relax_ms", "compute_ms", "relax_launches", "bytes_streamed",
                             "copy_ms", "kernel_launches", "edges_relaxed", "vertices_attempted",
                             "changes", "sweeps")}
 
@@ -622,6 +622,14 @@ def main():
                           "copy_busy_frac": copy_ms / 1e3 / dev_s if dev_s else 0},
         "pipeline_roofline": pipeline_roofline(relax_bytes, streamed, dev_s, hbm_peak, link),
         "relax": {"launches": relax_launches, "ms": relax_ms, "bytes": relax_bytes},
+        # where a step's device time goes (ms per step, CUDA events): the
+        # relax kernels, all kernels of the pipeline steps (gate, compaction,
+        # relax, PageRank apply), and the copies on the copy stream
+        "phases_ms_per_step": {
+            "device": 1e3 * dev_s / args.steps,
+            "relax": relax_ms / args.steps,
+            "step_kernels": sum(s1["compute_ms"] + s2["compute_ms"] for s1, s2 in stats) / args.steps,
+            "copies": copy_ms / args.steps},
         "gpu_launches": int(sum(a["kernel_launches"] + b["kernel_launches"] for a, b in stats)),
         "clocks": clk.summary(),
         "wall_s_timed": wall,
