@@ -415,8 +415,8 @@ int seraph_run(seraph_graph* g, const seraph_params* p, void* out_values, int ou
  * source >= n, the CSC check above), SERAPH_EOVERFLOW, SERAPH_ECUDA.
  *
  * The first call on each device resolves the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the scratch array and each clears it on entry, so calls
+ * (cudaGetSymbolAddress).  Every pass ends with a host read of its change
+ * count, so a call returns only once its fixpoint is reached.  All calls share the scratch array and each clears it on entry, so calls
  * that overlap on the GPU race: serialise them.
  */
 #define SERAPH_NOALLOC_MAX_VERTICES (1u << 20)

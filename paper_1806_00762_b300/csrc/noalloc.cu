@@ -15,7 +15,7 @@
 // counters and the list length are cleared at the start of every call, and
 // two calls that overlap on the GPU (different streams or threads) race.
 // The first call on each device resolves the array's device address with
-// cudaGetSymbolAddress; make that first call before any stream capture.
+// cudaGetSymbolAddress.
 #include <algorithm>
 #include <mutex>
 
