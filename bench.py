@@ -676,6 +676,12 @@ def main():
                        dict(sched["pagerank"], pr_normalize=1)))
         ladder.append(("resident+pvu+hybrid+pr_unit_sum+sor+push", dict(nopush, push=1),
                        dict(sched["pagerank"], pr_normalize=1)))
+        # every rung so far streams plain chunks as they are stored; the last
+        # adds the compact transfer of plain chunks (the benchmark default)
+        plain_xfer = lambda d: {k: v for k, v in d.items() if k != "stream_packed"}
+        ladder = [(nm, plain_xfer(ks), plain_xfer(kp)) for nm, ks, kp in ladder]
+        ladder.append(("resident+pvu+hybrid+pr_unit_sum+sor+push+compact_transfer", sched["sssp"],
+                       dict(sched["pagerank"], pr_normalize=1)))
         line["ablation"] = {}
         for name, ks, kp in ladder:
             a1, a2 = step(ks, kp)
