@@ -384,10 +384,12 @@ def main_batch(args, world, rank):
     # its query sources and its distances are read back into pinned host
     # memory on a copy stream while the next step computes
     srcs = [s for _, _, s in queries]
-    douts = [[torch.empty(graphs[g].n, dtype=torch.int32, device="cuda") for g, _, _ in queries]
-             for _ in range(2)]
+    sizes = [graphs[g].n for g, _, _ in queries]
+    # each plan's outputs are views of one device block, read back in one copy
+    blocks = [torch.empty(sum(sizes), dtype=torch.int32, device="cuda") for _ in range(2)]
+    douts = [list(torch.split(b, sizes)) for b in blocks]
     plans = [seraph.BatchPlan(graphs, queries, d, **kw) for d in douts]
-    houts = [torch.empty(graphs[g].n, dtype=torch.int32, pin_memory=True) for g, _, _ in queries]
+    hblock = torch.empty(sum(sizes), dtype=torch.int32, pin_memory=True)
     read_back = torch.cuda.Stream()
     read_done = [None, None]
     for pl in plans:
@@ -400,8 +402,7 @@ def main_batch(args, world, rank):
             read_done[k].synchronize()
         plans[k].run(srcs)
         with torch.cuda.stream(read_back):
-            for h, d in zip(houts, douts[k]):
-                h.copy_(d, non_blocking=True)
+            hblock.copy_(blocks[k], non_blocking=True)
         ev = torch.cuda.Event()
         ev.record(read_back)
         read_done[k] = ev
