@@ -318,11 +318,13 @@ typedef struct seraph_params {
     uint32_t stream_packed;     /* 1 (graphs built with SERAPH_COMPRESS): a
                                    chunk processed in the plain form streams
                                    compact into the far end of its ring slot
-                                   -- per page a header of two bytes per
-                                   vertex (in-degree, LEB128 code bytes;
-                                   larger counts in an escape list) with the
-                                   offsets of every 256th vertex, then the
-                                   page's gap stream -- and is rebuilt on the
+                                   -- per page a header of one bit per vertex
+                                   (has an in-edge) and two bytes per vertex
+                                   that has one (in-degree, LEB128 code
+                                   bytes; larger counts in an escape list)
+                                   with the offsets of every 256th vertex,
+                                   then the page's gap stream -- and is
+                                   rebuilt on the
                                    device into the plain form, page by page
                                    (each page's plain bytes end before its
                                    staged bytes start), so the host link

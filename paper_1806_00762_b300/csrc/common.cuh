@@ -216,7 +216,12 @@ constexpr uint32_t kStreamTile = 256;
 __host__ __device__ inline uint64_t stream_ckpt_bytes(uint64_t nv) {
     return 16 * ((nv + kStreamTile - 1) / kStreamTile + 1);
 }
-__host__ __device__ inline uint64_t stream_hdr_bytes(uint64_t nv) { return (2 * nv + 15) & ~15ull; }
+// one bit per vertex: set when it has an in-edge (32 bytes per tile)
+__host__ __device__ inline uint64_t stream_bitmap_bytes(uint64_t nv) {
+    return 32 * ((nv + kStreamTile - 1) / kStreamTile);
+}
+// two bytes per vertex with an in-edge
+__host__ __device__ inline uint64_t stream_hdr_bytes(uint64_t nnz) { return (2 * nnz + 15) & ~15ull; }
 __host__ __device__ inline uint64_t stream_esc_bytes(uint64_t nesc) { return (8 * nesc + 15) & ~15ull; }
 
 }  // namespace seraph

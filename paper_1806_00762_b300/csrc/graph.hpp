@@ -56,15 +56,19 @@ struct PageMeta {
     // Streamed header of the packed page (SERAPH_COMPRESS), in its own region,
     // sent ahead of the page's gap stream when a plain page streams compact:
     //   uint4 ckpt[T+1], T = ceil(nv / kStreamTile): (off, boff, escapes
-    //     before) at vertex t * kStreamTile, and (ne, gap-stream bytes, nesc);
-    //   u16 hdr[nv]: in-degree | code bytes << 8 when both are at most 254,
-    //     else 0xFFFF and the two counts are the vertex's escape entry;
+    //     before, vertices with an in-edge before) at vertex t * kStreamTile,
+    //     and (ne, gap-stream bytes, nesc, nnz) at the end;
+    //   u32 bits[T][8]: bit i of a tile set when its vertex i has an in-edge;
+    //   u16 hdr[nnz]: for each vertex with an in-edge, in order, in-degree |
+    //     code bytes << 8 when both are at most 254, else 0xFFFF and the two
+    //     counts are the vertex's escape entry;
     //   uint2 esc[nesc]: (in-degree, code bytes) of the escaped vertices in
     //     vertex order;
     // hdr and esc each padded to 16 B.
     uint64_t sh_off;    // byte offset of the header in the header region
     uint64_t sh_bytes;  // header bytes (multiple of 16)
     uint32_t sh_nesc;   // escaped vertices
+    uint32_t sh_nnz;    // vertices with an in-edge
 };
 
 

@@ -811,11 +811,12 @@ void for_pages(uint32_t P, F f) {
 }
 
 // The header that a packed page streams with when a plain chunk is sent in
-// compact form (PageMeta::sh_*): per vertex two bytes (in-degree, code
-// bytes) instead of the two u32 offsets, plus the offsets of every
-// kStreamTile-th vertex, so the device rebuilds both offset arrays one tile
-// per CTA without a page-wide scan.  Read from the packed pages' own off and
-// boff arrays, on the host.
+// compact form (PageMeta::sh_*): per vertex one bit (has an in-edge) and,
+// for the vertices that have one, two bytes (in-degree, code bytes) instead
+// of the two u32 offsets, plus the offsets of every kStreamTile-th vertex, so
+// the device rebuilds both offset arrays one tile per CTA without a
+// page-wide scan.  Read from the packed pages' own off and boff arrays, on
+// the host.
 static void build_stream_headers(seraph_graph* g) {
     const uint32_t P = g->num_pages;
     auto arrays = [&](const PageMeta& pm, const uint32_t*& off, const uint32_t*& boff) {
@@ -827,10 +828,16 @@ static void build_stream_headers(seraph_graph* g) {
         PageMeta& pm = g->pages[p];
         const uint32_t *off, *boff;
         arrays(pm, off, boff);
-        uint32_t nesc = 0;
-        for (uint64_t v = 0; v < pm.nv; ++v) nesc += escaped(off[v + 1] - off[v], boff[v + 1] - boff[v]);
+        uint32_t nesc = 0, nnz = 0;
+        for (uint64_t v = 0; v < pm.nv; ++v) {
+            const uint32_t d = off[v + 1] - off[v];
+            nnz += d > 0;
+            nesc += escaped(d, boff[v + 1] - boff[v]);
+        }
         pm.sh_nesc = nesc;
-        pm.sh_bytes = stream_ckpt_bytes(pm.nv) + stream_hdr_bytes(pm.nv) + stream_esc_bytes(nesc);
+        pm.sh_nnz = nnz;
+        pm.sh_bytes = stream_ckpt_bytes(pm.nv) + stream_bitmap_bytes(pm.nv) + stream_hdr_bytes(nnz) +
+                      stream_esc_bytes(nesc);
     });
     uint64_t total = 0;
     for (uint32_t p = 0; p < P; ++p) {
@@ -845,26 +852,32 @@ static void build_stream_headers(seraph_graph* g) {
         uint8_t* h = g->h_shdr.p + pm.sh_off;
         std::memset(h, 0, pm.sh_bytes);
         uint32_t* ck = (uint32_t*)h;
-        uint16_t* hd = (uint16_t*)(h + stream_ckpt_bytes(pm.nv));
-        uint32_t* es = (uint32_t*)(h + stream_ckpt_bytes(pm.nv) + stream_hdr_bytes(pm.nv));
-        uint32_t ne = 0;
+        uint32_t* bits = (uint32_t*)(h + stream_ckpt_bytes(pm.nv));
+        uint16_t* hd = (uint16_t*)(h + stream_ckpt_bytes(pm.nv) + stream_bitmap_bytes(pm.nv));
+        uint32_t* es = (uint32_t*)(h + stream_ckpt_bytes(pm.nv) + stream_bitmap_bytes(pm.nv) +
+                                   stream_hdr_bytes(pm.sh_nnz));
+        uint32_t ne = 0, nz = 0;
         for (uint64_t v = 0; v <= pm.nv; ++v) {
             if (v % kStreamTile == 0 || v == pm.nv) {
                 const uint64_t t = (v + kStreamTile - 1) / kStreamTile;  // v / tile, or T at the end
                 ck[4 * t] = off[v];
                 ck[4 * t + 1] = boff[v];
                 ck[4 * t + 2] = ne;
+                ck[4 * t + 3] = nz;
             }
             if (v == pm.nv) break;
             const uint32_t d = off[v + 1] - off[v], l = boff[v + 1] - boff[v];
+            if (d == 0) continue;
+            bits[v / 32] |= 1u << (v % 32);
             if (escaped(d, l)) {
-                hd[v] = 0xFFFFu;
+                hd[nz] = 0xFFFFu;
                 es[2 * ne] = d;
                 es[2 * ne + 1] = l;
                 ++ne;
             } else {
-                hd[v] = (uint16_t)(d | (l << 8));
+                hd[nz] = (uint16_t)(d | (l << 8));
             }
+            ++nz;
         }
     });
 }

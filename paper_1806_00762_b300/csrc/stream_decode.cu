@@ -82,8 +82,9 @@ __device__ __forceinline__ void decode_warp(const uint8_t* d, uint32_t* col, uin
 // in-degree and code bytes, escapes; layout in common.cuh) followed by its
 // gap stream; `out` = its plain form (off, col with zero padding, s_bytes in
 // all).  The regions must not overlap.  A CTA takes a tile of kStreamTile
-// vertices, one per thread: the escaped vertices find their entries by a
-// count of the escapes before them, a block scan of (in-degree, code bytes)
+// vertices, one per thread: a vertex with an in-edge finds its header entry
+// by a count of the tile's set bits before it, an escaped vertex its escape
+// entry by a count of the escapes before it, a block scan of (in-degree, code bytes)
 // from the tile's checkpoint gives each vertex's edge and byte offsets, and
 // each warp then decodes its 32 vertices.  Offsets are clamped to the page's
 // totals, so a damaged header cannot move a read or a write off the page.
@@ -95,14 +96,16 @@ __global__ void __launch_bounds__(kNT) decode_page_kernel(const uint8_t* __restr
     __shared__ unsigned long long ws[kNT / 32 + 1];
     __shared__ unsigned s_esc[kNT / 32];
     const uint4* ck = (const uint4*)in;
-    const uint64_t ckb = stream_ckpt_bytes(nv), hb = stream_hdr_bytes(nv);
-    const uint16_t* hdr = (const uint16_t*)(in + ckb);
-    const uint2* esc = (const uint2*)(in + ckb + hb);
-    const uint8_t* d = in + ckb + hb + stream_esc_bytes(nesc);
-    uint32_t* ooff = (uint32_t*)out;
-    uint32_t* col = (uint32_t*)(out + off_bytes);
     const uint32_t T = (nv + kStreamTile - 1) / kStreamTile;
     const uint4 last = ck[T];
+    const uint32_t nnz = last.w;
+    const uint64_t ckb = stream_ckpt_bytes(nv), bb = stream_bitmap_bytes(nv), hb = stream_hdr_bytes(nnz);
+    const uint32_t* bits = (const uint32_t*)(in + ckb);
+    const uint16_t* hdr = (const uint16_t*)(in + ckb + bb);
+    const uint2* esc = (const uint2*)(in + ckb + bb + hb);
+    const uint8_t* d = in + ckb + bb + hb + stream_esc_bytes(nesc);
+    uint32_t* ooff = (uint32_t*)out;
+    uint32_t* col = (uint32_t*)(out + off_bytes);
     const uint32_t ne = min(last.x, (uint32_t)((s_bytes - off_bytes) / 4)), nb = last.y;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     // the last offset and the zero padding of both arrays (a padding column
@@ -115,7 +118,12 @@ __global__ void __launch_bounds__(kNT) decode_page_kernel(const uint8_t* __restr
         const uint4 c0 = ck[t];
         const uint32_t v = t * kStreamTile + threadIdx.x;
         const bool valid = v < nv;
-        const uint32_t h = valid ? hdr[v] : 0u;
+        // this vertex's header entry: the tile's set bits before it
+        const uint32_t* tb = bits + 8 * (uint64_t)t;
+        const uint32_t word = tb[warp];
+        uint32_t hi = c0.w + __popc(word & lanemask_lt());
+        for (uint32_t w = 0; w < warp; ++w) hi += __popc(tb[w]);
+        const uint32_t h = valid && ((word >> lane) & 1u) && hi < nnz ? hdr[hi] : 0u;
         const bool x = h == 0xFFFFu;
         const unsigned m = __ballot_sync(kFull, x);
         if (lane == 0) s_esc[warp] = __popc(m);
