@@ -45,7 +45,7 @@ METRIC = "time-to-fixpoint and effective GTEPS, RMAT-28 streamed; learned vs fix
 
 DEFAULT_SSSP = ("order=cyclic,window=1,slots=16,pvu=strong,verify=0,columns=hybrid,push=1,"
                 "stream_packed=1")
-DEFAULT_PAGERANK = ("order=zigzag,window=1,slots=14,pvu=weak,columns=hybrid,pr_normalize=1,"
+DEFAULT_PAGERANK = ("order=cyclic,window=1,slots=14,pvu=weak,columns=hybrid,pr_normalize=1,"
                     "pr_omega=1.15,stream_packed=1")
 
 

@@ -4,7 +4,7 @@ The graph is built the way the benchmark builds its R-MAT-28 graph -- raw
 R-MAT edges generated on the device, vertices renumbered by out-degree
 (SERAPH_REORDER), every page kept both plain and packed (SERAPH_COMPRESS),
 512 destination-range pages -- and PageRank runs with the benchmark's own
-schedule string (zigzag order, one chunk per step, 14 ring slots, weak
+schedule string (cyclic order, one chunk per step, 14 ring slots, weak
 prediction, hybrid page forms, unit-sum scaling at sweep ends, steps
 over-relaxed by 1.15).  The edge budget is the benchmark's 16 GB scaled by the
 vertex count (2^(scale-28)), so the pages of a chunk and the packed share stay
