@@ -179,7 +179,7 @@ def build_graph(seraph, synth, torch, scale, pages, reorder=True, compress=True,
 # sweeps) -- weighted by the step's 154 PageRank and 64 SSSP relax launches
 # (profiles/relax_kernel_dram_rmat28.md); valid only for the kernel sources
 # (engine.cu and leb128.cuh) and the two schedules it was taken on.
-RELAX_TRAFFIC = {"kernel_sha256": "2c17ecc59c18a7bb", "bytes_per_launch": 6.4342e9,
+RELAX_TRAFFIC = {"kernel_sha256": "2c17ecc59c18a7bb", "bytes_per_launch": 6.4224e+09,
                  "sssp": DEFAULT_SSSP,
                  "pagerank": DEFAULT_PAGERANK,
                  "workload": "rmat28 default step"}
