@@ -1025,15 +1025,17 @@ int run_graph(seraph_graph* g, const seraph_params* P, void* out, int out_mem, s
             std::vector<uint32_t> ord(C);
             std::iota(ord.begin(), ord.end(), 0u);
             if (zig_base && (S.sweeps & 1)) std::reverse(ord.begin(), ord.end());
-            // SSSP/BFS/CC stream the chunks in order of predicted gain, the
-            // chunks already in the ring first (they cost no copy), so that the
-            // largest improvements propagate through the rest of the sweep;
-            // PageRank keeps the base order (forward Gauss-Seidel blocks)
+            // SSSP/BFS/CC: the chunks already in the ring first, in the base
+            // order (they cost no copy, and the base order -- out-degree order
+            // from the hubs -- is how improvements propagate); the chunks to
+            // be streamed after them in order of predicted gain (which
+            // partition to stream next).  PageRank keeps the base order
+            // (forward Gauss-Seidel blocks).
             if (!is_pr)
                 std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
                     const bool rx = slot_of[x] >= 0, ry = slot_of[y] >= 0;
                     if (rx != ry) return rx;
-                    return pr[x] > pr[y];
+                    return !rx && pr[x] > pr[y];
                 });
             // SSSP/BFS/CC: skip chunks predicted to change nothing, except after
             // a sweep without changes and at least every fourth sweep (the
